@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark: pJDS SpMV y = A x on one GB300 (and replicas on N GPUs).
+
+Workload (default): HMEp-like matrix after Sect. 1.3 of the paper, N = 6.2M,
+~15 nonzeros per row (7 fixed diagonals at 0, ±1, ±64, ±4096 plus symmetric
+random entries within |j-i| <= N/8), fp64 values, pJDS with b = 32. A step is
+one y = A x in the original basis (y scattered through the permutation), with
+the matrix and x resident in HBM. L2 is flushed (256 MB write) between timed
+steps; each step is timed with CUDA events on the launching stream.
+
+Throughput is reported in GB/s of algorithmic traffic, the paper's
+code-balance view (Eq. 1 with ideal RHS reuse): 8+4 bytes per nonzero for
+val+col, 8 bytes per element for x read once and y written once, 4 bytes per
+row for the permutation: 12 nnz + 20 N bytes (fp64). GF/s = 2 nnz / time.
+
+Side measurements in the same run: ELLPACK-R (the paper's baseline), pJDS with
+fp32 and bf16 values, the permuted-basis product, and the end-to-end call from
+pinned host memory. The CPU baseline is the fp64 oracle on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       (N > 1: launch with torch.distributed.run, one replica per GPU)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pJDS spMVM GB/s (% HBM roofline) & GF/s vs ELLPACK-R; mixed vs FP64 at stated err"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM bytes per launch of the timed pJDS kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload; valid only
+# while the kernel sources hash to the recorded value.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1112_5588_gb300", "csrc")
+    for name in ("spmv_kernels.cuh", "spmv_launch.cuh", "api.cu"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def alg_bytes(n_rows, n_cols, nnz, val_bytes, vec_bytes, scatter=True):
+    """Algorithmic bytes of one y = A x (ideal x reuse, y written once)."""
+    return nnz * (val_bytes + 4) + n_cols * vec_bytes + n_rows * vec_bytes + (4 * n_rows if scatter else 0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.index = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k + 1].lower() == "active"})
+        loaded = [r[0] for r in rows if r[0] > 0.5 * r[1]] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def gpu_id_for_smi(torch, dev) -> str:
+    """nvidia-smi --id for the torch device: its UUID when torch exposes it."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index or 0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=6_200_000, help="rows of the HMEp-like matrix")
+    ap.add_argument("--seed", type=int, default=1234)
+    ap.add_argument("--no-side", action="store_true", help="skip the side measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local_rank)
+
+
+def workload_desc(n):
+    return (f"HMEp-like (Holstein-Hubbard stand-in, Sect. 1.3): N={n}, diagonals 0,±1,±64,±4096 + symmetric "
+            f"random entries within |j-i|<=N/8, ~15 nnz/row; pJDS b=32, fp64, original basis")
+
+
+def build_matrix(args):
+    import synth
+    synth.build()
+    A = synth.hmep_like(n=args.n, seed=args.seed)
+    x = synth.vector(A.n_cols, seed=args.seed)
+    return A, x
+
+
+def run_reference(args, world, rank):
+    """The oracle (fp64 CRS, OpenMP on the host cores) as the reference arm."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    A, x = build_matrix(args)
+    cores = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.crs_spmv(A, x)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.crs_spmv(A, x)
+        times.append(time.perf_counter() - t0)
+    nbytes = alg_bytes(A.n_rows, A.n_cols, A.nnz, 8, 8)
+    t = sum(times)
+    value = nbytes * args.steps / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(A.n_rows), "n_rows": A.n_rows, "nnz": A.nnz,
+                       "parallelism": "host OpenMP"},
+            "gflops": round(2 * A.nnz * args.steps / t / 1e9, 3),
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"full matrix, one CRS y=Ax per step ({A.nnz} nnz)"},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_launches(torch, launch, steps, warmup, flush):
+    """Per-launch device time (s) with CUDA events on the current stream; L2
+    flushed before every launch (outside the events)."""
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        launch()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        if flush is not None:
+            flush.add_(1)
+        ev[k][0].record(s)
+        launch()
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in ev]
+
+
+def run_ours(args, world, rank, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1112_5588_gb300 import pjds
+
+    dist_on = world > 1
+    if dist_on:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank if dist_on else 0)
+    torch.cuda.set_device(dev)
+
+    t_gen = time.perf_counter()
+    A, x = build_matrix(args)
+    t_gen = time.perf_counter() - t_gen
+    t_conv = time.perf_counter()
+    H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64")
+    t_conv = time.perf_counter() - t_conv
+    D = H.to_device(dev)
+    perm_host = H.perm.copy()
+    n_stored = H.n_stored
+    H.destroy()
+    xt = torch.from_numpy(x).to(dev)
+    y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    nbytes = alg_bytes(A.n_rows, A.n_cols, A.nnz, 8, 8)
+
+    def barrier():
+        if dist_on:
+            dist.barrier()
+
+    # ---------------- main timed region: K pJDS fp64 products
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id_for_smi(torch, dev)) as clk:
+        durs = time_launches(torch, lambda: pjds.pjds_spmv(D, xt, y), args.steps, args.warmup, flush)
+        barrier()
+        torch.cuda.synchronize()
+    gpu_launches = args.steps
+    t_total = sum(durs)
+    if dist_on:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = nbytes * args.steps * world / t_total / 1e9
+    per_launch = t_total / args.steps
+    peak, peak_kind = hbm_peak()
+    achieved = nbytes / (sum(durs) / len(durs)) / 1e9
+    y_gpu = y.cpu().numpy()
+
+    side = {}
+    if not args.no_side:
+        side = side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes)
+
+    # ---------------- end to end through the C ABI from pinned host memory
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty(A.n_rows, dtype=torch.float64).pin_memory()
+    xd = torch.empty_like(xt)
+    yd = torch.empty_like(y)
+    for _ in range(args.warmup):
+        pjds.pjds_spmv_host(D, xh, yh, xd, yd)
+    barrier()
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pjds.pjds_spmv_host(D, xh, yh, xd, yd)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist_on:
+        tt = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    e2e_value = nbytes * args.steps * world / e2e_total / 1e9
+
+    if rank != 0:
+        if dist_on:
+            dist.destroy_process_group()
+        return 0
+
+    # ---------------- CPU baseline: the fp64 oracle on the host cores (rank 0, N = 1)
+    cpu = None
+    err = None
+    if world == 1:
+        import oracle
+        oracle.build()
+        cores = oracle.max_threads()
+        y_ref = oracle.crs_spmv(A, x)
+        reps, t_cpu = 0, 0.0
+        while t_cpu < args.cpu_seconds and reps < 1000:
+            t0 = time.perf_counter()
+            y_ref = oracle.crs_spmv(A, x)
+            t_cpu += time.perf_counter() - t0
+            reps += 1
+        cpu = {"value": round(nbytes * reps / t_cpu / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"full matrix ({A.nnz} nnz), {reps} CRS products in {t_cpu:.1f} s",
+               "gflops": round(2 * A.nnz * reps / t_cpu / 1e9, 3)}
+        absax = oracle.crs_absmv(A, x)
+        err = float(np.max(np.abs(y_gpu - y_ref)) / np.max(absax))
+
+    src_hash = kernel_source_hash()
+    tr = NCU_TRAFFIC.get(("hmep_f64_pjds", A.n_rows))
+    traffic = tr["bytes"] if tr and tr["src"] == src_hash else None
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(per_launch * 1e3, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(A.n_rows), "n_rows": A.n_rows, "nnz": A.nnz, "n_stored": n_stored,
+                   "b": 32, "alg_bytes_per_step": nbytes, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "seed": args.seed},
+        "gflops": round(2 * A.nnz * args.steps * world / t_total / 1e9, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "pjds_rows_kernel<double,double,int,1,8,true>", "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": 8 * A.n_cols,
+                "d2h_bytes_per_step": 8 * A.n_rows},
+        "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+        "error_fp64_normwise": err,
+        "setup_s": {"generate": round(t_gen, 2), "pjds_create": round(t_conv, 2)},
+        "kernel_src": src_hash,
+        **side,
+    }
+    print(json.dumps(line), flush=True)
+    if dist_on:
+        dist.destroy_process_group()
+    return 0
+
+
+def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
+    """ELLPACK-R, reduced precision, permuted basis and an L2-warm figure."""
+    out = {}
+    K, W = max(5, args.steps // 2), 3
+    med = statistics.median
+
+    t = med(time_launches(torch, lambda: pjds.pjds_spmv(D, xt, y), K, W, None))
+    out["pjds_f64_l2_warm"] = {"gbs": round(nbytes / t / 1e9, 1), "us": round(t * 1e6, 2)}
+
+    E = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype="f64")
+    ell_stored = E.n_stored
+    ED = E.to_device(dev)
+    E.destroy()
+    ye = torch.empty_like(y)
+    t_e = med(time_launches(torch, lambda: pjds.ellr_spmv(ED, xt, ye), K, W, flush))
+    t_p = med(time_launches(torch, lambda: pjds.pjds_spmv(D, xt, y), K, W, flush))
+    ell_bytes = alg_bytes(A.n_rows, A.n_cols, A.nnz, 8, 8, scatter=False) + 4 * A.n_rows
+    out["ellr_f64"] = {"gbs": round(ell_bytes / t_e / 1e9, 1), "gflops": round(2 * A.nnz / t_e / 1e9, 2),
+                       "us": round(t_e * 1e6, 2), "n_stored": ell_stored,
+                       "bit_identical_to_pjds": bool(torch.equal(ye, y))}
+    out["pjds_f64_median"] = {"gbs": round(nbytes / t_p / 1e9, 1), "gflops": round(2 * A.nnz / t_p / 1e9, 2),
+                              "us": round(t_p * 1e6, 2)}
+    out["pjds_vs_ellr_speed"] = round(t_e / t_p, 3)
+    out["pjds_data_reduction_vs_ellpack"] = round(1 - D.n_stored / ell_stored, 4)
+    del ED, ye
+
+    for dt in ("f32", "bf16"):
+        Hr = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dt)
+        Dr = Hr.to_device(dev)
+        Hr.destroy()
+        xr = xt.float()
+        yr = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
+        tr = med(time_launches(torch, lambda: pjds.pjds_spmv(Dr, xr, yr), K, W, flush))
+        vb = 4 if dt == "f32" else 2
+        b_r = alg_bytes(A.n_rows, A.n_cols, A.nnz, vb, 4)
+        dy = (yr.double() - y).abs().max().item()
+        out[f"pjds_{dt}"] = {"gbs": round(b_r / tr / 1e9, 1), "gflops": round(2 * A.nnz / tr / 1e9, 2),
+                             "us": round(tr * 1e6, 2), "speedup_vs_f64": round(t_p / tr, 3),
+                             "max_abs_diff_vs_f64_gpu": dy}
+        del Dr, xr, yr
+
+    Hp = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64", permute_cols=True)
+    Dp = Hp.to_device(dev)
+    Hp.destroy()
+    xp = torch.empty_like(xt)
+    yp = torch.empty_like(y)
+    pjds.pjds_permute(Dp, xt, xp)
+    t_pm = med(time_launches(torch, lambda: pjds.pjds_spmv(Dp, xp, yp), K, W, flush))
+    b_pm = alg_bytes(A.n_rows, A.n_cols, A.nnz, 8, 8, scatter=False)
+    out["pjds_f64_permuted_basis"] = {"gbs": round(b_pm / t_pm / 1e9, 1), "us": round(t_pm * 1e6, 2)}
+    del Dp, xp, yp
+
+    for cfg in ({"rows_per_thread": 2}, {"rows_per_thread": 4}, {"threads_per_row": 2}, {"block_threads": 512},
+                {"block_threads": 128}):
+        tc = med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xt, y, **cfg), K, W, flush))
+        key = "cfg_" + "_".join(f"{k}{v}" for k, v in cfg.items())
+        out[key] = {"gbs": round(nbytes / tc / 1e9, 1), "us": round(tc * 1e6, 2)}
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"side": out}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * pjds.h — C ABI of libpjds: sparse matrix-vector multiplication y = A x on a
+ * GB300 (sm_103a) with A stored in padded jagged diagonals storage (pJDS), and
+ * the ELLPACK-R format as the baseline.
+ *
+ * Paper: M. Kreutzer, G. Hager, G. Wellein, H. Fehske, A. Basermann,
+ * A. R. Bishop, "Sparse matrix-vector multiplication on GPGPU clusters: A new
+ * storage format and a scalable implementation", arXiv:1112.5588.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PJDS_OK (0) or a negative status below. pjds_last_error()
+ *     returns a message for the last failure on the calling thread. Nothing
+ *     aborts, no C++ exception crosses this boundary, and no error is signalled
+ *     by a device fault.
+ *   - Host arrays passed in are borrowed for the duration of the call only.
+ *   - Device memory is never allocated by this library: every device pointer
+ *     is owned by the caller (e.g. a torch tensor's data_ptr()).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Kernel launches are asynchronous on that stream; a launch
+ *     error is reported as PJDS_ECUDA, execution errors surface at the
+ *     caller's next synchronisation.
+ *   - Indices are 0-based. Matrices have at most 2^31-1 rows and columns.
+ */
+#ifndef PJDS_H
+#define PJDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PJDS_OK 0
+#define PJDS_EINVAL (-1)    /* null pointer, bad size, bad b, malformed CRS, dtype mismatch, misalignment */
+#define PJDS_ENOMEM (-2)    /* host allocation failed */
+#define PJDS_ECUDA (-3)     /* CUDA runtime error (launch configuration, copy) */
+#define PJDS_EOVERFLOW (-4) /* stored element count or an index does not fit the format */
+
+/* Storage type of the matrix values. Vectors x, y are double for PJDS_F64 and
+ * float for PJDS_F32 and PJDS_BF16; products are accumulated in the vector
+ * type (Table 1 compares single and double precision; BF16 halves the value
+ * bytes again). */
+typedef enum pjds_dtype { PJDS_F64 = 0, PJDS_F32 = 1, PJDS_BF16 = 2 } pjds_dtype;
+
+/* Message for the last failing call on this thread ("" if none). The pointer
+ * stays valid until the next call on the same thread. */
+const char *pjds_last_error(void);
+
+/* Library ABI version (increments when a struct layout changes). */
+int32_t pjds_version(void);
+
+/* sizeof of the ABI structs, for bindings to check their layouts:
+ * out[0..4] = pjds_host, pjds_dev, pjds_launch, ellr_host, ellr_dev. */
+void pjds_abi_sizes(int32_t out[5]);
+
+/* ------------------------------------------------------------------------ */
+/* pJDS (Sect. 2.1, Listing 2)                                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Host-side pJDS arrays, created by pjds_create and owned by the library
+ * until pjds_destroy. Layout (Sect. 2.1):
+ *   - rows are sorted by descending length, equal lengths keeping their
+ *     original order: perm[new] = old, inv_perm[old] = new;
+ *   - rows are padded to n_pad = ceil(n_rows / b) * b with empty rows;
+ *   - each block of b consecutive sorted rows is padded to its longest row,
+ *     block_len[k] (non-increasing in k);
+ *   - row_len[i] is the length of sorted row i (0 for padding rows);
+ *   - the padded matrix is stored column by column ("jagged diagonals"):
+ *     entry j of sorted row i sits at col_start[j] + i, for j < block_len of
+ *     its block; col_start has n_max + 1 entries, col_start[n_max] = n_stored;
+ *   - padding entries hold value +0 and column index -1.
+ * With permute_cols = 1 the column indices are renumbered into the permuted
+ * basis (col -> inv_perm[col]; square matrices only), the form in which an
+ * iterative solver runs entirely on permuted vectors (Sect. 2.1).
+ * val holds n_stored elements of dtype (double, float, or bfloat16 as uint16
+ * bits, rounded to nearest even from the fp64 input).
+ */
+typedef struct pjds_host {
+  int32_t n_rows, n_cols, n_pad, b, n_blocks, n_max;
+  int64_t nnz, n_stored;
+  int32_t dtype, permute_cols;
+  int32_t *perm;      /* [n_rows]   */
+  int32_t *inv_perm;  /* [n_rows]   */
+  int32_t *block_len; /* [n_blocks] */
+  int32_t *row_len;   /* [n_pad]    */
+  int64_t *col_start; /* [n_max+1]  */
+  int32_t *col;       /* [n_stored] */
+  void *val;          /* [n_stored] of dtype */
+} pjds_host;
+
+/*
+ * Device-side view of the same arrays: the caller copies each host array into
+ * a device buffer it owns and fills this struct (sizes copied from the host
+ * struct). row_len and inv_perm are not read by the kernels and may be NULL.
+ * val must be 16-byte aligned; all other pointers 4-byte aligned.
+ */
+typedef struct pjds_dev {
+  int32_t n_rows, n_cols, n_pad, b, n_blocks, n_max;
+  int64_t nnz, n_stored;
+  int32_t dtype, permute_cols;
+  const int32_t *perm;
+  const int32_t *block_len;
+  const int32_t *row_len;
+  const int64_t *col_start;
+  const int32_t *col;
+  const void *val;
+} pjds_dev;
+
+/*
+ * Convert a CRS matrix (row_ptr[n_rows+1] int64, col_idx[nnz] int32 in
+ * [0, n_cols), val[nnz] fp64; columns within a row are kept in the given
+ * order, which fixes the summation order) into pJDS with block size b.
+ * b must be a positive multiple of 32 (the warp width, Sect. 2.1: "b_r should
+ * be the warp size"). On success *out receives a new handle.
+ * Errors: PJDS_EINVAL (null pointers, n_rows < 0, n_cols < 1, bad b, row_ptr not
+ * starting at 0 or decreasing, a column out of range, permute_cols on a
+ * non-square matrix, unknown dtype), PJDS_ENOMEM, PJDS_EOVERFLOW.
+ */
+int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
+                const double *val, int32_t b, int32_t dtype, int32_t permute_cols, pjds_host **out);
+
+/* Free a handle from pjds_create (NULL is accepted). */
+int pjds_destroy(pjds_host *h);
+
+/*
+ * y = A x with A in pJDS (Listing 2): one thread per sorted row i computes
+ * sum_{j < len(i)} val[col_start[j] + i] * x[col[col_start[j] + i]] in the
+ * row's original entry order with fused multiply-add, then
+ *   - permute_cols = 0: writes y[perm[i]] (x and y in the original basis);
+ *   - permute_cols = 1: writes y[i] (x and y in the permuted basis).
+ * x: n_cols elements, y: n_rows elements, device memory of the vector type of
+ * A->dtype; x and y must not overlap. Every element of y is written.
+ */
+int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
+
+/*
+ * Kernel configuration for pjds_spmv_cfg (tuning and autotuning):
+ *   rows_per_thread  1, 2 or 4 adjacent sorted rows per thread, read with one
+ *                    vector load per jagged diagonal (0 = default);
+ *   threads_per_row  1, 2, 4 or 8 threads share one row, splitting its jagged
+ *                    diagonals round-robin and adding partial sums at the end
+ *                    (sliced ELLR-T style; changes the summation order);
+ *   block_threads    threads per CTA, a multiple of 32 in [32, 512]
+ *                    (0 = default).
+ * rows_per_thread > 1 and threads_per_row > 1 are exclusive.
+ */
+typedef struct pjds_launch {
+  int32_t rows_per_thread;
+  int32_t threads_per_row;
+  int32_t block_threads;
+  int32_t reserved;
+} pjds_launch;
+
+int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
+
+/*
+ * End-to-end product from host memory: copies x_host (n_cols elements) into
+ * the caller's device buffer x_dev, runs pjds_spmv into y_dev, copies y_dev
+ * back into y_host (n_rows elements) and waits for the stream. Host buffers
+ * should be pinned for full copy bandwidth.
+ */
+int pjds_spmv_host(const pjds_dev *A, const void *x_host, void *y_host, void *x_dev, void *y_dev, void *stream);
+
+/*
+ * Basis changes around an iterative solver (Sect. 2.1): for i < n_rows,
+ *   pjds_permute:   v_perm[i] = v[perm[i]]   (original -> permuted basis)
+ *   pjds_unpermute: v[perm[i]] = v_perm[i]   (permuted -> original basis)
+ * Vectors are device memory of A's vector type and must not overlap.
+ */
+int pjds_permute(const pjds_dev *A, const void *v, void *v_perm, void *stream);
+int pjds_unpermute(const pjds_dev *A, const void *v_perm, void *v, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* ELLPACK-R (Sect. 2.1, Listing 1)                                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Host-side ELLPACK-R arrays, owned by the library until ellr_destroy. Rows
+ * keep their original order and are padded to n_pad = ceil(n_rows/32)*32
+ * (footnote to Sect. 2.1); each row's entries are shifted left into an
+ * n_pad x n_max rectangle stored column by column: entry j of row i at
+ * j * n_pad + i. row_max[i] is the length of row i (0 for padding rows);
+ * padding entries hold value +0 and column -1.
+ */
+typedef struct ellr_host {
+  int32_t n_rows, n_cols, n_pad, n_max;
+  int64_t nnz, n_stored;
+  int32_t dtype, reserved;
+  int32_t *row_max; /* [n_pad]    */
+  int32_t *col;     /* [n_stored] */
+  void *val;        /* [n_stored] of dtype */
+} ellr_host;
+
+typedef struct ellr_dev {
+  int32_t n_rows, n_cols, n_pad, n_max;
+  int64_t nnz, n_stored;
+  int32_t dtype, reserved;
+  const int32_t *row_max;
+  const int32_t *col;
+  const void *val;
+} ellr_dev;
+
+/* Convert CRS to ELLPACK-R. Same arguments and errors as pjds_create. */
+int ellr_create(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
+                const double *val, int32_t dtype, ellr_host **out);
+
+int ellr_destroy(ellr_host *h);
+
+/*
+ * y = A x with A in ELLPACK-R (Listing 1): one thread per row i computes
+ * sum_{j < row_max[i]} val[j*n_pad + i] * x[col[j*n_pad + i]] with fused
+ * multiply-add and writes y[i]. Same vector conventions as pjds_spmv.
+ */
+int ellr_spmv(const ellr_dev *A, const void *x, void *y, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PJDS_H */

@@ -1,0 +1,155 @@
+// C entry points for the device products (pjds_spmv*, ellr_spmv, basis
+// changes): argument checks, the default kernel configuration, dtype dispatch.
+#include <stdint.h>
+
+#include "common.h"
+#include "spmv_launch.cuh"
+
+namespace pjds {
+
+static int check_pjds_dev(const pjds_dev *A, const void *x, const void *y) {
+  if (!A) return set_error(PJDS_EINVAL, "A is NULL");
+  if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "unknown dtype %d", A->dtype);
+  if (A->n_rows < 0 || A->n_cols < 1 || A->b <= 0 || A->b % 32 != 0)
+    return set_error(PJDS_EINVAL, "bad sizes (n_rows %d, n_cols %d, b %d)", A->n_rows, A->n_cols, A->b);
+  if ((int64_t)A->n_pad != ((int64_t)A->n_rows + A->b - 1) / A->b * A->b || A->n_blocks != A->n_pad / A->b)
+    return set_error(PJDS_EINVAL, "n_pad/n_blocks inconsistent with n_rows and b");
+  if (A->n_rows > 0 && (!x || !y)) return set_error(PJDS_EINVAL, "x or y is NULL");
+  if (A->n_stored > 0 && (!A->val || !A->col || !A->col_start || !A->block_len))
+    return set_error(PJDS_EINVAL, "a matrix array is NULL");
+  if (A->n_rows > 0 && !A->permute_cols && !A->perm) return set_error(PJDS_EINVAL, "perm is NULL");
+  if (A->permute_cols && A->n_rows != A->n_cols) return set_error(PJDS_EINVAL, "permuted basis needs a square matrix");
+  return PJDS_OK;
+}
+
+static int dispatch_pjds(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s) {
+  if (A->n_rows == 0) return PJDS_OK;
+  if (A->n_stored == 0) {
+    // no stored entries: every row sum is zero
+    cudaError_t e = cudaMemsetAsync(y, 0, (size_t)A->n_rows * vector_bytes(A->dtype), s);
+    return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  switch (A->dtype) {
+    case PJDS_F64: return pjds_launch_f64(A, x, y, c, s);
+    case PJDS_F32: return pjds_launch_f32(A, x, y, c, s);
+    default: return pjds_launch_bf16(A, x, y, c, s);
+  }
+}
+
+static int check_cfg(const pjds_dev *A, const LaunchCfg &c) {
+  const int R = c.rows_per_thread, T = c.threads_per_row;
+  if (R != 1 && R != 2 && R != 4) return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
+  if (T != 1 && T != 2 && T != 4 && T != 8) return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
+  if (R > 1 && T > 1) return set_error(PJDS_EINVAL, "rows_per_thread > 1 needs threads_per_row = 1");
+  if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32)
+    return set_error(PJDS_EINVAL, "block_threads must be a multiple of 32 in [32, 512]");
+  if (R > 1) {
+    const uintptr_t va = (uintptr_t)A->val, ca = (uintptr_t)A->col;
+    const int vb = value_bytes(A->dtype) * R, need_v = vb < 16 ? vb : 16, need_c = 4 * R < 16 ? 4 * R : 16;
+    if (va % need_v || ca % need_c)
+      return set_error(PJDS_EINVAL, "val/col not aligned for %d-row vector loads", R);
+  }
+  return PJDS_OK;
+}
+
+// Default configuration: one thread per row (the paper's mapping), 256
+// threads per CTA.
+static LaunchCfg default_cfg(const pjds_dev *A) {
+  (void)A;
+  LaunchCfg c;
+  c.rows_per_thread = 1;
+  c.threads_per_row = 1;
+  c.block_threads = 256;
+  return c;
+}
+
+}  // namespace pjds
+
+using namespace pjds;
+
+extern "C" int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream) {
+  clear_error();
+  int rc = check_pjds_dev(A, x, y);
+  if (rc) return rc;
+  const LaunchCfg c = default_cfg(A);
+  rc = check_cfg(A, c);
+  if (rc) return rc;
+  return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream) {
+  clear_error();
+  int rc = check_pjds_dev(A, x, y);
+  if (rc) return rc;
+  LaunchCfg c = default_cfg(A);
+  if (cfg) {
+    if (cfg->rows_per_thread) c.rows_per_thread = cfg->rows_per_thread;
+    if (cfg->threads_per_row) c.threads_per_row = cfg->threads_per_row;
+    if (cfg->block_threads) c.block_threads = cfg->block_threads;
+  }
+  rc = check_cfg(A, c);
+  if (rc) return rc;
+  return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pjds_spmv_host(const pjds_dev *A, const void *x_host, void *y_host, void *x_dev, void *y_dev,
+                              void *stream) {
+  clear_error();
+  int rc = check_pjds_dev(A, x_dev, y_dev);
+  if (rc) return rc;
+  if (A->n_rows > 0 && (!x_host || !y_host)) return set_error(PJDS_EINVAL, "host vector is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t vb = (size_t)vector_bytes(A->dtype);
+  if (A->n_rows > 0) {
+    cudaError_t e = cudaMemcpyAsync(x_dev, x_host, (size_t)A->n_cols * vb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "copy x to device: %s", cudaGetErrorString(e));
+    const LaunchCfg c = default_cfg(A);
+    rc = check_cfg(A, c);
+    if (rc) return rc;
+    rc = dispatch_pjds(A, x_dev, y_dev, c, s);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(y_host, y_dev, (size_t)A->n_rows * vb, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "copy y to host: %s", cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+  return PJDS_OK;
+}
+
+static int permute_common(const pjds_dev *A, const void *src, void *dst, bool inverse, void *stream) {
+  clear_error();
+  if (!A) return set_error(PJDS_EINVAL, "A is NULL");
+  if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "unknown dtype %d", A->dtype);
+  if (A->n_rows < 0) return set_error(PJDS_EINVAL, "bad n_rows");
+  if (A->n_rows == 0) return PJDS_OK;
+  if (!A->perm || !src || !dst) return set_error(PJDS_EINVAL, "perm or a vector is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (A->dtype == PJDS_F64) return launch_permute<double>(A->perm, src, dst, A->n_rows, inverse, s);
+  return launch_permute<float>(A->perm, src, dst, A->n_rows, inverse, s);
+}
+
+extern "C" int pjds_permute(const pjds_dev *A, const void *v, void *v_perm, void *stream) {
+  return permute_common(A, v, v_perm, false, stream);
+}
+
+extern "C" int pjds_unpermute(const pjds_dev *A, const void *v_perm, void *v, void *stream) {
+  return permute_common(A, v_perm, v, true, stream);
+}
+
+extern "C" int ellr_spmv(const ellr_dev *A, const void *x, void *y, void *stream) {
+  clear_error();
+  if (!A) return set_error(PJDS_EINVAL, "A is NULL");
+  if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "unknown dtype %d", A->dtype);
+  if (A->n_rows < 0 || A->n_cols < 1 || (int64_t)A->n_pad != ((int64_t)A->n_rows + 31) / 32 * 32)
+    return set_error(PJDS_EINVAL, "bad sizes");
+  if (A->n_rows == 0) return PJDS_OK;
+  if (!x || !y || !A->row_max) return set_error(PJDS_EINVAL, "x, y or row_max is NULL");
+  if (A->n_stored > 0 && (!A->val || !A->col)) return set_error(PJDS_EINVAL, "val or col is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nt = 256;
+  switch (A->dtype) {
+    case PJDS_F64: return ellr_launch_f64(A, x, y, nt, s);
+    case PJDS_F32: return ellr_launch_f32(A, x, y, nt, s);
+    default: return ellr_launch_bf16(A, x, y, nt, s);
+  }
+}

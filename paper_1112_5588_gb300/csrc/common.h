@@ -1,0 +1,28 @@
+// Internal declarations shared by the host converter and the CUDA entry points.
+#pragma once
+
+#include <stdint.h>
+
+#include "pjds.h"
+
+namespace pjds {
+
+// Record a message for pjds_last_error() on this thread and return `code`.
+int set_error(int code, const char *fmt, ...)
+#if defined(__GNUC__)
+    __attribute__((format(printf, 2, 3)))
+#endif
+    ;
+
+// Clear the thread's message (called at the start of every entry point).
+void clear_error();
+
+// Bytes of one stored value of the given dtype (0 for an unknown dtype).
+inline int value_bytes(int32_t dtype) {
+  return dtype == PJDS_F64 ? 8 : (dtype == PJDS_F32 || dtype == PJDS_BF16) ? (dtype == PJDS_F32 ? 4 : 2) : 0;
+}
+
+// Bytes of one vector element (x, y) for the given dtype.
+inline int vector_bytes(int32_t dtype) { return dtype == PJDS_F64 ? 8 : 4; }
+
+}  // namespace pjds

@@ -1,0 +1,14 @@
+// Kernel instances for f32 values (float vectors and accumulation).
+#include "spmv_launch.cuh"
+
+namespace pjds {
+
+int pjds_launch_f32(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s) {
+  return launch_pjds<float, float>(A, x, y, c, s);
+}
+
+int ellr_launch_f32(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s) {
+  return launch_ellr<float, float>(A, x, y, nt, s);
+}
+
+}  // namespace pjds

@@ -1,0 +1,14 @@
+// Kernel instances for f64 values (double vectors and accumulation).
+#include "spmv_launch.cuh"
+
+namespace pjds {
+
+int pjds_launch_f64(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s) {
+  return launch_pjds<double, double>(A, x, y, c, s);
+}
+
+int ellr_launch_f64(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s) {
+  return launch_ellr<double, double>(A, x, y, nt, s);
+}
+
+}  // namespace pjds

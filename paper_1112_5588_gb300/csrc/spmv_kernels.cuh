@@ -1,0 +1,308 @@
+// pJDS and ELLPACK-R SpMV kernels for sm_103a (GB300).
+//
+// The product is bound by HBM bandwidth (about 0.15 flop per byte in fp64),
+// not by arithmetic, and it is not a dense contraction, so there is no
+// tensor-core path. What matters is keeping enough bytes in flight:
+//   - val[] and col[] are streamed once: loads carry the evict-first hint in
+//     L1 and L2 (ld.global.cs) so they do not push x out of the caches;
+//   - a warp reads one jagged diagonal as one contiguous run (Listing 2
+//     addressing col_start[j] + i), with optional 2- or 4-row vector loads;
+//   - the gather x[col] goes through the read-only L1 path (ld.global.nc);
+//   - the j-loop is unrolled so each thread issues U independent val/col
+//     loads, then U gathers, before the dependent fused multiply-adds;
+//   - the accumulator stays in a register and y is written once (scattered
+//     through perm[] in the original basis).
+// Pad entries carry column -1 and are skipped, so every row's sum runs over
+// exactly its own entries in CRS order, as in Listing 2.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pjds {
+namespace dev {
+
+// ----------------------------------------------------------------------------- value / vector types
+
+struct bf16_t {
+  uint16_t bits;
+};
+
+template <typename TV>
+struct Acc;
+template <>
+struct Acc<double> {
+  using T = double;
+};
+template <>
+struct Acc<float> {
+  using T = float;
+};
+template <>
+struct Acc<bf16_t> {
+  using T = float;
+};
+
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ float to_acc(bf16_t v) { return __uint_as_float(((uint32_t)v.bits) << 16); }
+
+__device__ __forceinline__ double fma_acc(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_acc(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// ----------------------------------------------------------------------------- streaming loads
+
+// R consecutive elements from a 16-byte-or-less aligned run, evict-first.
+template <int R>
+__device__ __forceinline__ void ld_stream(const double *p, double (&v)[R]) {
+  if constexpr (R == 1) {
+    v[0] = __ldcs(p);
+  } else if constexpr (R == 2) {
+    double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+  } else {
+    double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void ld_stream(const float *p, float (&v)[R]) {
+  if constexpr (R == 1) {
+    v[0] = __ldcs(p);
+  } else if constexpr (R == 2) {
+    float2 a = __ldcs(reinterpret_cast<const float2 *>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+  } else {
+    float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void ld_stream(const bf16_t *p, bf16_t (&v)[R]) {
+  if constexpr (R == 1) {
+    v[0].bits = __ldcs(reinterpret_cast<const unsigned short *>(p));
+  } else if constexpr (R == 2) {
+    unsigned int a = __ldcs(reinterpret_cast<const unsigned int *>(p));
+    v[0].bits = (uint16_t)(a & 0xFFFFu);
+    v[1].bits = (uint16_t)(a >> 16);
+  } else {
+    uint2 a = __ldcs(reinterpret_cast<const uint2 *>(p));
+    v[0].bits = (uint16_t)(a.x & 0xFFFFu);
+    v[1].bits = (uint16_t)(a.x >> 16);
+    v[2].bits = (uint16_t)(a.y & 0xFFFFu);
+    v[3].bits = (uint16_t)(a.y >> 16);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void ld_stream(const int32_t *p, int32_t (&v)[R]) {
+  if constexpr (R == 1) {
+    v[0] = __ldcs(p);
+  } else if constexpr (R == 2) {
+    int2 a = __ldcs(reinterpret_cast<const int2 *>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+  } else {
+    int4 a = __ldcs(reinterpret_cast<const int4 *>(p));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+  }
+}
+
+__device__ __forceinline__ double ld_stream1(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream1(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ bf16_t ld_stream1(const bf16_t *p) {
+  bf16_t v;
+  v.bits = __ldcs(reinterpret_cast<const unsigned short *>(p));
+  return v;
+}
+
+// Gather through the read-only L1 path; pads (c < 0) read nothing.
+template <typename TX>
+__device__ __forceinline__ TX gather(const TX *__restrict__ x, int32_t c) {
+  return c >= 0 ? __ldg(x + c) : TX(0);
+}
+
+// ----------------------------------------------------------------------------- pJDS, R rows per thread
+
+// Thread t owns sorted rows [R*t, R*t + R) of one block (b is a multiple of
+// 32 >= R). Loop bound: the block's padded length; pads are skipped.
+template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER>
+__global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
+                                                         const int64_t *__restrict__ col_start,
+                                                         const int32_t *__restrict__ block_len,
+                                                         const int32_t *__restrict__ perm, const TX *__restrict__ x,
+                                                         TX *__restrict__ y, int32_t n_rows, int32_t n_pad, int32_t b) {
+  using TA = typename Acc<TV>::T;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i0 = t * R;
+  if (i0 >= n_pad) return;
+  const int32_t L = __ldg(block_len + (int32_t)(i0 / b));
+  TA acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = TA(0);
+
+  int32_t j = 0;
+  for (; j + U <= L; j += U) {
+    int32_t c[U][R];
+    TV v[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i0;
+      ld_stream<R>(col + o, c[u]);
+      ld_stream<R>(val + o, v[u]);
+    }
+    TX xv[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r) xv[u][r] = gather(x, c[u][r]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        acc[r] = c[u][r] >= 0 ? fma_acc(to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
+  }
+  for (; j < L; ++j) {
+    int32_t c[R];
+    TV v[R];
+    const IDX o = (IDX)__ldg(col_start + j) + (IDX)i0;
+    ld_stream<R>(col + o, c);
+    ld_stream<R>(val + o, v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const TX xv = gather(x, c[r]);
+      acc[r] = c[r] >= 0 ? fma_acc(to_acc(v[r]), (TA)xv, acc[r]) : acc[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = i0 + r;
+    if (i < n_rows) {
+      if constexpr (SCATTER)
+        y[__ldcs(perm + i)] = (TX)acc[r];
+      else
+        y[i] = (TX)acc[r];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- pJDS, T threads per row
+
+// T consecutive lanes share one sorted row: lane s takes jagged diagonals
+// j = s, s+T, ...; the T partial sums are added with shuffles (fixed tree).
+template <typename TV, typename TX, typename IDX, int T, int U, bool SCATTER>
+__global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
+                                                        const int64_t *__restrict__ col_start,
+                                                        const int32_t *__restrict__ block_len,
+                                                        const int32_t *__restrict__ perm, const TX *__restrict__ x,
+                                                        TX *__restrict__ y, int32_t n_rows, int32_t n_pad, int32_t b) {
+  using TA = typename Acc<TV>::T;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = g / T;
+  const int32_t s = (int32_t)(g % T);
+  const bool active = i < n_pad;  // whole warps stay for the shuffles
+  const int32_t L = active ? __ldg(block_len + (int32_t)(i / b)) : 0;
+  TA acc = TA(0);
+  int32_t j = s;
+  for (; j + (U - 1) * T < L; j += U * T) {
+    int32_t c[U];
+    TV v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const IDX o = (IDX)__ldg(col_start + j + u * T) + (IDX)i;
+      c[u] = __ldcs(col + o);
+      v[u] = ld_stream1(val + o);
+    }
+    TX xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = gather(x, c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? fma_acc(to_acc(v[u]), (TA)xv[u], acc) : acc;
+  }
+  for (; j < L; j += T) {
+    const IDX o = (IDX)__ldg(col_start + j) + (IDX)i;
+    const int32_t c = __ldcs(col + o);
+    const TV v = ld_stream1(val + o);
+    const TX xv = gather(x, c);
+    acc = c >= 0 ? fma_acc(to_acc(v), (TA)xv, acc) : acc;
+  }
+#pragma unroll
+  for (int off = T / 2; off >= 1; off /= 2) acc += __shfl_down_sync(0xffffffffu, acc, off, T);
+  if (s == 0 && i < n_rows) {
+    if constexpr (SCATTER)
+      y[__ldcs(perm + i)] = (TX)acc;
+    else
+      y[i] = (TX)acc;
+  }
+}
+
+// ----------------------------------------------------------------------------- ELLPACK-R (Listing 1)
+
+// One thread per row in the original order; loop to the row's own length.
+template <typename TV, typename TX, typename IDX, int U>
+__global__ void __launch_bounds__(512) ellr_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
+                                                    const int32_t *__restrict__ row_max, const TX *__restrict__ x,
+                                                    TX *__restrict__ y, int32_t n_rows, int32_t n_pad) {
+  using TA = typename Acc<TV>::T;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rows) return;
+  const int32_t L = __ldcs(row_max + i);
+  TA acc = TA(0);
+  int32_t j = 0;
+  for (; j + U <= L; j += U) {
+    int32_t c[U];
+    TV v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const IDX o = (IDX)(j + u) * (IDX)n_pad + (IDX)i;
+      c[u] = __ldcs(col + o);
+      v[u] = ld_stream1(val + o);
+    }
+    TX xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = fma_acc(to_acc(v[u]), (TA)xv[u], acc);
+  }
+  for (; j < L; ++j) {
+    const IDX o = (IDX)j * (IDX)n_pad + (IDX)i;
+    const int32_t c = __ldcs(col + o);
+    const TV v = ld_stream1(val + o);
+    acc = fma_acc(to_acc(v), (TA)__ldg(x + c), acc);
+  }
+  y[i] = (TX)acc;
+}
+
+// ----------------------------------------------------------------------------- basis changes
+
+template <typename TX>
+__global__ void permute_kernel(const int32_t *__restrict__ perm, const TX *__restrict__ v, TX *__restrict__ vp,
+                               int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) vp[i] = __ldg(v + __ldcs(perm + i));
+}
+
+template <typename TX>
+__global__ void unpermute_kernel(const int32_t *__restrict__ perm, const TX *__restrict__ vp, TX *__restrict__ v,
+                                 int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[__ldcs(perm + i)] = __ldcs(vp + i);
+}
+
+}  // namespace dev
+}  // namespace pjds

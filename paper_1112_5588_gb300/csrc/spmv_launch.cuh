@@ -1,0 +1,103 @@
+// Typed launchers: pick the kernel instance for (value type, index width,
+// rows per thread, threads per row, scatter) and launch it on a stream.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "spmv_kernels.cuh"
+
+namespace pjds {
+
+struct LaunchCfg {
+  int rows_per_thread;  // R: 1, 2, 4
+  int threads_per_row;  // T: 1, 2, 4, 8
+  int block_threads;    // CTA size
+};
+
+// Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
+inline int check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  return PJDS_OK;
+}
+
+template <typename TV, typename TX, typename IDX, bool SC>
+int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaStream_t s) {
+  const TV *val = static_cast<const TV *>(A->val);
+  const int R = c.rows_per_thread, T = c.threads_per_row, nt = c.block_threads;
+  const int64_t work = T > 1 ? (int64_t)A->n_pad * T : ((int64_t)A->n_pad + R - 1) / R;
+  const int64_t grid = (work + nt - 1) / nt;
+  if (grid <= 0) return PJDS_OK;
+  if (grid > 0x7fffffffLL) return set_error(PJDS_EOVERFLOW, "grid too large");
+  const dim3 g((unsigned)grid), blk((unsigned)nt);
+#define PJDS_ARGS val, A->col, A->col_start, A->block_len, A->perm, x, y, A->n_rows, A->n_pad, A->b
+  if (T == 1) {
+    switch (R) {
+      case 1: dev::pjds_rows_kernel<TV, TX, IDX, 1, 8, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
+      case 2: dev::pjds_rows_kernel<TV, TX, IDX, 2, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
+      case 4: dev::pjds_rows_kernel<TV, TX, IDX, 4, 2, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
+      default: return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
+    }
+  } else {
+    switch (T) {
+      case 2: dev::pjds_tpr_kernel<TV, TX, IDX, 2, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
+      case 4: dev::pjds_tpr_kernel<TV, TX, IDX, 4, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
+      case 8: dev::pjds_tpr_kernel<TV, TX, IDX, 8, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
+      default: return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
+    }
+  }
+#undef PJDS_ARGS
+  return check_launch("pjds_spmv launch");
+}
+
+template <typename TV, typename TX>
+int launch_pjds(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s) {
+  const TX *xx = static_cast<const TX *>(x);
+  TX *yy = static_cast<TX *>(y);
+  const bool small = A->n_stored + A->n_pad < 0x7fffffffLL;
+  const bool scatter = !A->permute_cols;
+  if (small)
+    return scatter ? launch_pjds_idx<TV, TX, int32_t, true>(A, xx, yy, c, s)
+                   : launch_pjds_idx<TV, TX, int32_t, false>(A, xx, yy, c, s);
+  return scatter ? launch_pjds_idx<TV, TX, int64_t, true>(A, xx, yy, c, s)
+                 : launch_pjds_idx<TV, TX, int64_t, false>(A, xx, yy, c, s);
+}
+
+template <typename TV, typename TX>
+int launch_ellr(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s) {
+  const int64_t grid = ((int64_t)A->n_rows + nt - 1) / nt;
+  if (grid <= 0) return PJDS_OK;
+  const TV *val = static_cast<const TV *>(A->val);
+  const TX *xx = static_cast<const TX *>(x);
+  TX *yy = static_cast<TX *>(y);
+  if (A->n_stored < 0x7fffffffLL)
+    dev::ellr_kernel<TV, TX, int32_t, 8>
+        <<<(unsigned)grid, nt, 0, s>>>(val, A->col, A->row_max, xx, yy, A->n_rows, A->n_pad);
+  else
+    dev::ellr_kernel<TV, TX, int64_t, 8>
+        <<<(unsigned)grid, nt, 0, s>>>(val, A->col, A->row_max, xx, yy, A->n_rows, A->n_pad);
+  return check_launch("ellr_spmv launch");
+}
+
+template <typename TX>
+int launch_permute(const int32_t *perm, const void *src, void *dst, int32_t n, bool inverse, cudaStream_t s) {
+  const int nt = 256;
+  const int64_t grid = ((int64_t)n + nt - 1) / nt;
+  if (grid <= 0) return PJDS_OK;
+  if (inverse)
+    dev::unpermute_kernel<TX><<<(unsigned)grid, nt, 0, s>>>(perm, static_cast<const TX *>(src), static_cast<TX *>(dst), n);
+  else
+    dev::permute_kernel<TX><<<(unsigned)grid, nt, 0, s>>>(perm, static_cast<const TX *>(src), static_cast<TX *>(dst), n);
+  return check_launch("pjds_permute launch");
+}
+
+// Per-dtype entry points, each compiled in its own translation unit.
+int pjds_launch_f64(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s);
+int pjds_launch_f32(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s);
+int pjds_launch_bf16(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s);
+int ellr_launch_f64(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
+int ellr_launch_f32(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
+int ellr_launch_bf16(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
+
+}  // namespace pjds

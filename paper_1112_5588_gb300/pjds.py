@@ -1,0 +1,374 @@
+"""Python binding of libpjds (ctypes): argument marshalling only.
+
+Names follow the C ABI in include/pjds.h. Every step of the product runs in the
+library's CUDA kernels; this module only moves host arrays into torch device
+tensors, fills the ABI structs and passes pointers and the current torch stream.
+There is no CPU fallback: if libpjds.so is missing, importing this module fails.
+
+Typical use::
+
+    H = pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64")
+    D = H.to_device("cuda")          # torch-owned device buffers
+    y = torch.empty(H.n_rows, dtype=D.vec_dtype, device="cuda")
+    pjds_spmv(D, x, y)               # y = A x on the current stream
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpjds.so")
+
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
+_VEC_TORCH = {0: torch.float64, 1: torch.float32, 2: torch.float32}
+_VAL_NP = {0: np.float64, 1: np.float32, 2: np.uint16}
+_VAL_BYTES = {0: 8, 1: 4, 2: 2}
+
+_i32, _i64, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+
+class PjdsError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+class _PjdsHostS(ctypes.Structure):
+    _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
+                ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
+                ("perm", _vp), ("inv_perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp),
+                ("col", _vp), ("val", _vp)]
+
+
+class _PjdsDevS(ctypes.Structure):
+    _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
+                ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
+                ("perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp), ("col", _vp),
+                ("val", _vp)]
+
+
+class _LaunchS(ctypes.Structure):
+    _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("reserved", _i32)]
+
+
+class _EllrHostS(ctypes.Structure):
+    _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("n_max", _i32), ("nnz", _i64),
+                ("n_stored", _i64), ("dtype", _i32), ("reserved", _i32), ("row_max", _vp), ("col", _vp),
+                ("val", _vp)]
+
+
+class _EllrDevS(ctypes.Structure):
+    _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("n_max", _i32), ("nnz", _i64),
+                ("n_stored", _i64), ("dtype", _i32), ("reserved", _i32), ("row_max", _vp), ("col", _vp),
+                ("val", _vp)]
+
+
+def _load_lib():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1112_5588_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "pjds_last_error": (ctypes.c_char_p, []),
+        "pjds_version": (_i32, []),
+        "pjds_abi_sizes": (None, [_vp]),
+        "pjds_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, P(P(_PjdsHostS))]),
+        "pjds_destroy": (ctypes.c_int, [P(_PjdsHostS)]),
+        "pjds_spmv": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
+        "pjds_spmv_cfg": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, P(_LaunchS), _vp]),
+        "pjds_spmv_host": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp, _vp, _vp]),
+        "pjds_permute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
+        "pjds_unpermute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
+        "ellr_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, P(P(_EllrHostS))]),
+        "ellr_destroy": (ctypes.c_int, [P(_EllrHostS)]),
+        "ellr_spmv": (ctypes.c_int, [P(_EllrDevS), _vp, _vp, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    sizes = (ctypes.c_int32 * 5)()
+    lib.pjds_abi_sizes(sizes)
+    want = [ctypes.sizeof(s) for s in (_PjdsHostS, _PjdsDevS, _LaunchS, _EllrHostS, _EllrDevS)]
+    if list(sizes) != want:
+        raise ImportError(f"libpjds ABI struct sizes {list(sizes)} differ from the binding's {want}")
+    return lib
+
+
+_lib = _load_lib()
+
+
+def lib():
+    """The loaded ctypes library (for tests that call the C ABI directly)."""
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise PjdsError(rc, where, _lib.pjds_last_error().decode(errors="replace"))
+
+
+def _dtype_code(dtype) -> int:
+    if isinstance(dtype, str):
+        if dtype not in DTYPES:
+            raise ValueError(f"dtype must be one of {sorted(DTYPES)}")
+        return DTYPES[dtype]
+    return int(dtype)
+
+
+def _np_view(ptr, n, np_dtype):
+    n = int(n)
+    if n == 0 or not ptr:
+        return np.zeros(0, np_dtype)
+    buf = (ctypes.c_char * (n * np.dtype(np_dtype).itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=np_dtype, count=n)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _crs_args(row_ptr, col, val):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    return rp, c, v
+
+
+# --------------------------------------------------------------------------- pJDS
+
+class PjdsHost:
+    """pJDS arrays owned by the library (pjds_host); numpy views stay valid
+    until destroy()."""
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+        s = ptr.contents
+        for f, _ in _PjdsHostS._fields_[:10]:
+            setattr(self, f, int(getattr(s, f)))
+        self.perm = _np_view(s.perm, s.n_rows, np.int32)
+        self.inv_perm = _np_view(s.inv_perm, s.n_rows, np.int32)
+        self.block_len = _np_view(s.block_len, s.n_blocks, np.int32)
+        self.row_len = _np_view(s.row_len, s.n_pad, np.int32)
+        self.col_start = _np_view(s.col_start, s.n_max + 1, np.int64)
+        self.col = _np_view(s.col, s.n_stored, np.int32)
+        self.val = _np_view(s.val, s.n_stored, _VAL_NP[s.dtype])
+
+    def arrays(self) -> dict:
+        """Copies of every array plus the sizes (survive destroy())."""
+        out = {k: getattr(self, k) for k, _ in _PjdsHostS._fields_[:10]}
+        for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val"):
+            out[k] = getattr(self, k).copy()
+        return out
+
+    def to_device(self, device="cuda") -> "PjdsDevice":
+        return PjdsDevice(self, device)
+
+    def destroy(self):
+        if self._ptr is not None:
+            _lib.pjds_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def pjds_create(n_rows: int, n_cols: int, row_ptr, col, val, b: int = 32, dtype="f64",
+                permute_cols: bool = False) -> PjdsHost:
+    """CRS -> pJDS on the host (pjds_create)."""
+    rp, c, v = _crs_args(row_ptr, col, val)
+    if len(rp) != n_rows + 1:
+        raise ValueError("row_ptr must have n_rows + 1 entries")
+    out = ctypes.POINTER(_PjdsHostS)()
+    _check(_lib.pjds_create(n_rows, n_cols, rp.ctypes.data, c.ctypes.data, v.ctypes.data, b, _dtype_code(dtype),
+                            1 if permute_cols else 0, ctypes.byref(out)), "pjds_create")
+    return PjdsHost(out)
+
+
+class PjdsDevice:
+    """Device copy of a pJDS matrix in torch-owned buffers plus its pjds_dev struct."""
+
+    def __init__(self, host: PjdsHost, device="cuda"):
+        dev = torch.device(device)
+        self.device = dev
+        self.dtype = host.dtype
+        self.vec_dtype = _VEC_TORCH[host.dtype]
+        self.n_rows, self.n_cols, self.n_pad = host.n_rows, host.n_cols, host.n_pad
+        self.nnz, self.n_stored, self.b, self.n_max = host.nnz, host.n_stored, host.b, host.n_max
+        self.permute_cols = host.permute_cols
+
+        def up(a, np_dt):
+            return torch.from_numpy(np.ascontiguousarray(a).view(np_dt).copy()).to(dev)
+
+        self.perm = up(host.perm, np.int32)
+        self.block_len = up(host.block_len, np.int32)
+        self.row_len = up(host.row_len, np.int32)
+        self.col_start = up(host.col_start, np.int64)
+        self.col = up(host.col, np.int32)
+        self.val = up(host.val, {0: np.float64, 1: np.float32, 2: np.int16}[host.dtype])
+        s = _PjdsDevS()
+        for f, _ in _PjdsDevS._fields_[:10]:
+            setattr(s, f, getattr(host, f))
+        s.perm = self.perm.data_ptr() or None
+        s.block_len = self.block_len.data_ptr() or None
+        s.row_len = self.row_len.data_ptr() or None
+        s.col_start = self.col_start.data_ptr() or None
+        s.col = self.col.data_ptr() or None
+        s.val = self.val.data_ptr() or None
+        self._s = s
+
+    @property
+    def struct(self):
+        return self._s
+
+    def device_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.perm, self.block_len, self.row_len, self.col_start,
+                                                           self.col, self.val))
+
+
+def _check_vec(t: torch.Tensor, n: int, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor with {n} elements")
+
+
+def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """y = A x (pjds_spmv). Original basis unless A was built with permute_cols."""
+    _check_vec(x, A.n_cols, A.vec_dtype, "x")
+    _check_vec(y, A.n_rows, A.vec_dtype, "y")
+    _check(_lib.pjds_spmv(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), _stream_ptr(stream)), "pjds_spmv")
+    return y
+
+
+def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
+                  threads_per_row: int = 0, block_threads: int = 0, stream=None) -> torch.Tensor:
+    """y = A x with an explicit kernel configuration (pjds_spmv_cfg)."""
+    _check_vec(x, A.n_cols, A.vec_dtype, "x")
+    _check_vec(y, A.n_rows, A.vec_dtype, "y")
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, 0)
+    _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
+                              _stream_ptr(stream)), "pjds_spmv_cfg")
+    return y
+
+
+def pjds_spmv_host(A: PjdsDevice, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor,
+                   y_dev: torch.Tensor, stream=None) -> torch.Tensor:
+    """Host x -> device -> y = A x -> host y, synchronous (pjds_spmv_host)."""
+    for t, n, name in ((x_host, A.n_cols, "x_host"), (y_host, A.n_rows, "y_host")):
+        if t.device.type != "cpu" or t.dtype != A.vec_dtype or t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU {A.vec_dtype} tensor with {n} elements")
+    _check_vec(x_dev, A.n_cols, A.vec_dtype, "x_dev")
+    _check_vec(y_dev, A.n_rows, A.vec_dtype, "y_dev")
+    _check(_lib.pjds_spmv_host(ctypes.byref(A.struct), x_host.data_ptr(), y_host.data_ptr(), x_dev.data_ptr(),
+                               y_dev.data_ptr(), _stream_ptr(stream)), "pjds_spmv_host")
+    return y_host
+
+
+def pjds_permute(A: PjdsDevice, v: torch.Tensor, v_perm: torch.Tensor, stream=None) -> torch.Tensor:
+    """v_perm[i] = v[perm[i]] (original -> permuted basis)."""
+    _check_vec(v, A.n_rows, A.vec_dtype, "v")
+    _check_vec(v_perm, A.n_rows, A.vec_dtype, "v_perm")
+    _check(_lib.pjds_permute(ctypes.byref(A.struct), v.data_ptr(), v_perm.data_ptr(), _stream_ptr(stream)),
+           "pjds_permute")
+    return v_perm
+
+
+def pjds_unpermute(A: PjdsDevice, v_perm: torch.Tensor, v: torch.Tensor, stream=None) -> torch.Tensor:
+    """v[perm[i]] = v_perm[i] (permuted -> original basis)."""
+    _check_vec(v_perm, A.n_rows, A.vec_dtype, "v_perm")
+    _check_vec(v, A.n_rows, A.vec_dtype, "v")
+    _check(_lib.pjds_unpermute(ctypes.byref(A.struct), v_perm.data_ptr(), v.data_ptr(), _stream_ptr(stream)),
+           "pjds_unpermute")
+    return v
+
+
+# --------------------------------------------------------------------------- ELLPACK-R
+
+class EllrHost:
+    """ELLPACK-R arrays owned by the library (ellr_host)."""
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+        s = ptr.contents
+        for f, _ in _EllrHostS._fields_[:8]:
+            setattr(self, f, int(getattr(s, f)))
+        self.row_max = _np_view(s.row_max, s.n_pad, np.int32)
+        self.col = _np_view(s.col, s.n_stored, np.int32)
+        self.val = _np_view(s.val, s.n_stored, _VAL_NP[s.dtype])
+
+    def arrays(self) -> dict:
+        out = {k: getattr(self, k) for k, _ in _EllrHostS._fields_[:8]}
+        for k in ("row_max", "col", "val"):
+            out[k] = getattr(self, k).copy()
+        return out
+
+    def to_device(self, device="cuda") -> "EllrDevice":
+        return EllrDevice(self, device)
+
+    def destroy(self):
+        if self._ptr is not None:
+            _lib.ellr_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ellr_create(n_rows: int, n_cols: int, row_ptr, col, val, dtype="f64") -> EllrHost:
+    """CRS -> ELLPACK-R on the host (ellr_create)."""
+    rp, c, v = _crs_args(row_ptr, col, val)
+    if len(rp) != n_rows + 1:
+        raise ValueError("row_ptr must have n_rows + 1 entries")
+    out = ctypes.POINTER(_EllrHostS)()
+    _check(_lib.ellr_create(n_rows, n_cols, rp.ctypes.data, c.ctypes.data, v.ctypes.data, _dtype_code(dtype),
+                            ctypes.byref(out)), "ellr_create")
+    return EllrHost(out)
+
+
+class EllrDevice:
+    def __init__(self, host: EllrHost, device="cuda"):
+        dev = torch.device(device)
+        self.device = dev
+        self.dtype = host.dtype
+        self.vec_dtype = _VEC_TORCH[host.dtype]
+        self.n_rows, self.n_cols, self.n_pad, self.n_max = host.n_rows, host.n_cols, host.n_pad, host.n_max
+        self.nnz, self.n_stored = host.nnz, host.n_stored
+        vt = {0: torch.float64, 1: torch.float32, 2: torch.int16}[host.dtype]
+        npt = {torch.float64: np.float64, torch.float32: np.float32, torch.int16: np.int16}[vt]
+        self.row_max = torch.from_numpy(host.row_max.copy()).to(dev)
+        self.col = torch.from_numpy(host.col.copy()).to(dev)
+        self.val = torch.from_numpy(host.val.copy().view(npt)).to(dev)
+        s = _EllrDevS()
+        for f, _ in _EllrDevS._fields_[:8]:
+            setattr(s, f, getattr(host, f))
+        s.row_max = self.row_max.data_ptr() or None
+        s.col = self.col.data_ptr() or None
+        s.val = self.val.data_ptr() or None
+        self._s = s
+
+    @property
+    def struct(self):
+        return self._s
+
+
+def ellr_spmv(A: EllrDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """y = A x with A in ELLPACK-R (ellr_spmv)."""
+    _check_vec(x, A.n_cols, A.vec_dtype, "x")
+    _check_vec(y, A.n_rows, A.vec_dtype, "y")
+    _check(_lib.ellr_spmv(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), _stream_ptr(stream)), "ellr_spmv")
+    return y

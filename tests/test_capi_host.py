@@ -1,0 +1,172 @@
+"""C-ABI library on the host (no GPU): it loads, exports every declared symbol,
+and its CRS -> pJDS / ELLPACK-R conversion equals the oracle's bit for bit.
+Error paths return statuses, never abort."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from synth import tiny
+from tests.conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1112_5588_gb300 import build
+    build.build()
+    from paper_1112_5588_gb300 import pjds
+    return pjds
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        src = re.sub(r"#[^\n]*", "", src)
+        for m in re.finditer(r"\b([A-Za-z_]\w*)\s*\(([^;{}()]*(?:\([^()]*\))?[^;{}()]*)\)\s*;", src):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(P):
+    names = _declared_functions()
+    assert "pjds_spmv" in names and "ellr_create" in names and len(names) >= 12
+    lib = ctypes.CDLL(P.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_abi_version_and_struct_sizes(P):
+    assert P.lib().pjds_version() == 1  # the binding itself checked the struct sizes on load
+
+
+CASES = [
+    ("banded", lambda: synth.banded_uniform(n=4000, hw=500, seed=3)),
+    ("ragged", lambda: tiny.random_lengths(333, 120, max_len=60, seed=5, p_empty=0.2)),
+    ("rect_wide", lambda: tiny.random_lengths(70, 500, max_len=90, seed=6)),
+    ("rect_tall", lambda: tiny.random_lengths(900, 40, max_len=40, seed=7)),
+    ("one_full_row", lambda: tiny.one_full_row(130, full_row=77)),
+    ("zipf", lambda: synth.zipf_rows(5000, s=1.8, len_max=300, seed=8)),
+    ("empty_rows_only", lambda: tiny.from_lengths([0] * 45, 10)),
+    ("single_row", lambda: tiny.from_lengths([7], 9, seed=1)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("b", [32, 64, 256])
+def test_pjds_create_matches_oracle_bit_exact(P, oracle_lib, name, make, b):
+    A = make()
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b)
+    R = oracle_lib.pjds_convert(A, b=b)
+    for k in ("n_pad", "n_blocks", "n_max", "n_stored", "nnz"):
+        assert getattr(H, k) == R[k], k
+    for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col"):
+        assert np.array_equal(getattr(H, k), R[k]), k
+    assert np.array_equal(H.val.view(np.uint64), R["val"].view(np.uint64))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_pjds_create_reduced_precision_values(P, oracle_lib, dtype):
+    A = synth.hmep_like(n=20_000, seed=2)
+    # exercise ties, subnormals and overflow in the bf16 path as well
+    e = np.exp2
+    special = np.array([1 + e(-8), 1 + 3 * e(-8), 1 + e(-8) + e(-30), e(-133), e(-134), 3 * e(-134),
+                        e(128) - e(119), e(128) - e(120), -0.1, 1e-45, 3e38, -3.4e38])
+    val = A.val.copy()
+    val[:len(special)] = special
+    A = A._replace(val=val)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, val, b=32, dtype=dtype)
+    R = oracle_lib.pjds_convert(A, b=32)
+    want = oracle_lib.round_f32(R["val"]) if dtype == "f32" else oracle_lib.round_bf16(R["val"])
+    if dtype == "f32":
+        got = H.val.astype(np.float64)
+    else:
+        got = (H.val.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    assert np.array_equal(got, want)
+    assert np.array_equal(H.col, R["col"])
+
+
+def test_pjds_create_permuted_columns(P, oracle_lib):
+    A = synth.hmep_like(n=30_000, seed=4)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, permute_cols=True)
+    R = oracle_lib.pjds_convert(A, b=32, permute_cols=True)
+    assert np.array_equal(H.col, R["col"]) and np.array_equal(H.val, R["val"])
+
+
+@pytest.mark.parametrize("name,make", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_ellr_create_matches_oracle_bit_exact(P, oracle_lib, name, make):
+    A = make()
+    H = P.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val)
+    R = oracle_lib.ellr_convert(A, pad_to=32)
+    for k in ("n_pad", "n_max", "n_stored"):
+        assert getattr(H, k) == R[k], k
+    assert np.array_equal(H.row_max, R["row_max"])
+    assert np.array_equal(H.col, R["col"])
+    assert np.array_equal(H.val, R["val"])
+
+
+def test_storage_reduction_vs_ellpack(P):
+    # Sect. 2.1: pJDS never stores more than ELLPACK, and far less for a wide
+    # spread of row lengths.
+    A = synth.zipf_rows(20_000, s=2.0, len_max=512, seed=1)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    E = P.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val)
+    assert H.n_stored <= E.n_stored
+    assert 1 - H.n_stored / E.n_stored > 0.9
+
+
+def _status(P, fn, *args):
+    with pytest.raises(P.PjdsError) as ei:
+        fn(*args)
+    return ei.value.code
+
+
+def test_error_paths_return_status(P):
+    A = tiny.random_lengths(40, 30, max_len=10, seed=2)
+    EINVAL, EOVER = -1, -4
+    assert _status(P, P.pjds_create, A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, 48) == EINVAL  # b % 32
+    assert _status(P, P.pjds_create, A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, 0) == EINVAL
+    bad_col = A.col.copy()
+    bad_col[3] = A.n_cols
+    assert _status(P, P.pjds_create, A.n_rows, A.n_cols, A.row_ptr, bad_col, A.val, 32) == EINVAL
+    bad_rp = A.row_ptr.copy()
+    bad_rp[5] = bad_rp[6] + 1
+    assert _status(P, P.pjds_create, A.n_rows, A.n_cols, bad_rp, A.col, A.val, 32) == EINVAL
+    bad_rp = A.row_ptr.copy()
+    bad_rp[0] = 1
+    assert _status(P, P.ellr_create, A.n_rows, A.n_cols, bad_rp, A.col, A.val) == EINVAL
+    assert _status(P, P.pjds_create, A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, 32, 7) == EINVAL  # dtype
+    assert _status(P, P.pjds_create, A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, 32, "f64", True) == EINVAL
+    lib = P.lib()
+    assert lib.pjds_create(1, 1, None, None, None, 32, 0, 0, None) == EINVAL
+    assert lib.pjds_spmv(None, None, None, None) == EINVAL
+    assert lib.ellr_spmv(None, None, None, None) == EINVAL
+    assert lib.pjds_destroy(None) == 0
+    assert b"NULL" in lib.pjds_last_error() or lib.pjds_last_error() == b""
+    del EOVER
+
+
+def test_spmv_argument_checks_without_gpu(P):
+    # Invalid configurations are rejected on the host before any launch.
+    A = tiny.random_lengths(64, 64, max_len=8, seed=1)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    s = P._PjdsDevS()
+    for f, _ in P._PjdsDevS._fields_[:10]:
+        setattr(s, f, getattr(H, f))
+    lib = P.lib()
+    cfg = P._LaunchS(3, 1, 256, 0)
+    fake = ctypes.c_void_p(16)
+    s.val = s.col = s.col_start = s.block_len = s.perm = 256
+    assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
+    cfg = P._LaunchS(2, 2, 256, 0)
+    assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
+    cfg = P._LaunchS(1, 1, 1000, 0)
+    assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
+    s.n_pad = 33
+    assert lib.pjds_spmv(ctypes.byref(s), fake, fake, None) == -1
