@@ -142,14 +142,18 @@ int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
  *                    diagonals round-robin and adding partial sums at the end
  *                    (sliced ELLR-T style; changes the summation order);
  *   block_threads    threads per CTA, a multiple of 32 in [32, 512]
- *                    (0 = default).
- * rows_per_thread > 1 and threads_per_row > 1 are exclusive.
+ *                    (0 = default);
+ *   unroll           jagged diagonals loaded per round of the j-loop
+ *                    (0 = default; R=1: 4, 8, 16; R=2: 2, 4, 8; R=4: 2, 4;
+ *                    T>1: 2, 4).
+ * rows_per_thread > 1 and threads_per_row > 1 are exclusive. Invalid values
+ * return PJDS_EINVAL.
  */
 typedef struct pjds_launch {
   int32_t rows_per_thread;
   int32_t threads_per_row;
   int32_t block_threads;
-  int32_t reserved;
+  int32_t unroll;
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);

@@ -36,11 +36,12 @@ static int dispatch_pjds(const pjds_dev *A, const void *x, void *y, const Launch
   }
 }
 
-static int check_cfg(const pjds_dev *A, const LaunchCfg &c) {
+static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   const int R = c.rows_per_thread, T = c.threads_per_row;
   if (R != 1 && R != 2 && R != 4) return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
   if (T != 1 && T != 2 && T != 4 && T != 8) return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
   if (R > 1 && T > 1) return set_error(PJDS_EINVAL, "rows_per_thread > 1 needs threads_per_row = 1");
+  if (c.unroll == 0) c.unroll = R == 1 ? 8 : (R == 2 ? 4 : 2);
   if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32)
     return set_error(PJDS_EINVAL, "block_threads must be a multiple of 32 in [32, 512]");
   if (R > 1) {
@@ -60,6 +61,7 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   c.rows_per_thread = 1;
   c.threads_per_row = 1;
   c.block_threads = 256;
+  c.unroll = 0;
   return c;
 }
 
@@ -71,7 +73,7 @@ extern "C" int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream
   clear_error();
   int rc = check_pjds_dev(A, x, y);
   if (rc) return rc;
-  const LaunchCfg c = default_cfg(A);
+  LaunchCfg c = default_cfg(A);
   rc = check_cfg(A, c);
   if (rc) return rc;
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
@@ -86,6 +88,7 @@ extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pj
     if (cfg->rows_per_thread) c.rows_per_thread = cfg->rows_per_thread;
     if (cfg->threads_per_row) c.threads_per_row = cfg->threads_per_row;
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
+    if (cfg->unroll) c.unroll = cfg->unroll;
   }
   rc = check_cfg(A, c);
   if (rc) return rc;
@@ -103,7 +106,7 @@ extern "C" int pjds_spmv_host(const pjds_dev *A, const void *x_host, void *y_hos
   if (A->n_rows > 0) {
     cudaError_t e = cudaMemcpyAsync(x_dev, x_host, (size_t)A->n_cols * vb, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return set_error(PJDS_ECUDA, "copy x to device: %s", cudaGetErrorString(e));
-    const LaunchCfg c = default_cfg(A);
+    LaunchCfg c = default_cfg(A);
     rc = check_cfg(A, c);
     if (rc) return rc;
     rc = dispatch_pjds(A, x_dev, y_dev, c, s);

@@ -140,13 +140,15 @@ __device__ __forceinline__ TX gather(const TX *__restrict__ x, int32_t c) {
 // ----------------------------------------------------------------------------- pJDS, R rows per thread
 
 // Thread t owns sorted rows [R*t, R*t + R) of one block (b is a multiple of
-// 32 >= R). Loop bound: the block's padded length; pads are skipped.
+// 32 >= R). Loop bound: the block's padded length; pads are skipped. The
+// j-loop runs in chunks of U jagged diagonals; a chunk's loads are predicated
+// on j < L, so a short row issues all of its loads in ceil(L/U) rounds.
 template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER>
 __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
-                                                         const int64_t *__restrict__ col_start,
-                                                         const int32_t *__restrict__ block_len,
-                                                         const int32_t *__restrict__ perm, const TX *__restrict__ x,
-                                                         TX *__restrict__ y, int32_t n_rows, int32_t n_pad, int32_t b) {
+                                                        const int64_t *__restrict__ col_start,
+                                                        const int32_t *__restrict__ block_len,
+                                                        const int32_t *__restrict__ perm, const TX *__restrict__ x,
+                                                        TX *__restrict__ y, int32_t n_rows, int32_t n_pad, int32_t b) {
   using TA = typename Acc<TV>::T;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i0 = t * R;
@@ -156,15 +158,22 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = TA(0);
 
-  int32_t j = 0;
-  for (; j + U <= L; j += U) {
+  for (int32_t j = 0; j < L; j += U) {
     int32_t c[U][R];
     TV v[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i0;
-      ld_stream<R>(col + o, c[u]);
-      ld_stream<R>(val + o, v[u]);
+      if (j + u < L) {
+        const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i0;
+        ld_stream<R>(col + o, c[u]);
+        ld_stream<R>(val + o, v[u]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          c[u][r] = -1;
+          v[u][r] = TV{};
+        }
+      }
     }
     TX xv[U][R];
 #pragma unroll
@@ -176,18 +185,6 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
 #pragma unroll
       for (int r = 0; r < R; ++r)
         acc[r] = c[u][r] >= 0 ? fma_acc(to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
-  }
-  for (; j < L; ++j) {
-    int32_t c[R];
-    TV v[R];
-    const IDX o = (IDX)__ldg(col_start + j) + (IDX)i0;
-    ld_stream<R>(col + o, c);
-    ld_stream<R>(val + o, v);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const TX xv = gather(x, c[r]);
-      acc[r] = c[r] >= 0 ? fma_acc(to_acc(v[r]), (TA)xv, acc[r]) : acc[r];
-    }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -218,28 +215,25 @@ __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ va
   const bool active = i < n_pad;  // whole warps stay for the shuffles
   const int32_t L = active ? __ldg(block_len + (int32_t)(i / b)) : 0;
   TA acc = TA(0);
-  int32_t j = s;
-  for (; j + (U - 1) * T < L; j += U * T) {
+  for (int32_t j = s; j < L; j += U * T) {
     int32_t c[U];
     TV v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const IDX o = (IDX)__ldg(col_start + j + u * T) + (IDX)i;
-      c[u] = __ldcs(col + o);
-      v[u] = ld_stream1(val + o);
+      if (j + u * T < L) {
+        const IDX o = (IDX)__ldg(col_start + j + u * T) + (IDX)i;
+        c[u] = __ldcs(col + o);
+        v[u] = ld_stream1(val + o);
+      } else {
+        c[u] = -1;
+        v[u] = TV{};
+      }
     }
     TX xv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) xv[u] = gather(x, c[u]);
 #pragma unroll
     for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? fma_acc(to_acc(v[u]), (TA)xv[u], acc) : acc;
-  }
-  for (; j < L; j += T) {
-    const IDX o = (IDX)__ldg(col_start + j) + (IDX)i;
-    const int32_t c = __ldcs(col + o);
-    const TV v = ld_stream1(val + o);
-    const TX xv = gather(x, c);
-    acc = c >= 0 ? fma_acc(to_acc(v), (TA)xv, acc) : acc;
   }
 #pragma unroll
   for (int off = T / 2; off >= 1; off /= 2) acc += __shfl_down_sync(0xffffffffu, acc, off, T);
@@ -263,27 +257,25 @@ __global__ void __launch_bounds__(512) ellr_kernel(const TV *__restrict__ val, c
   if (i >= n_rows) return;
   const int32_t L = __ldcs(row_max + i);
   TA acc = TA(0);
-  int32_t j = 0;
-  for (; j + U <= L; j += U) {
+  for (int32_t j = 0; j < L; j += U) {
     int32_t c[U];
     TV v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const IDX o = (IDX)(j + u) * (IDX)n_pad + (IDX)i;
-      c[u] = __ldcs(col + o);
-      v[u] = ld_stream1(val + o);
+      if (j + u < L) {
+        const IDX o = (IDX)(j + u) * (IDX)n_pad + (IDX)i;
+        c[u] = __ldcs(col + o);
+        v[u] = ld_stream1(val + o);
+      } else {
+        c[u] = -1;
+        v[u] = TV{};
+      }
     }
     TX xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+    for (int u = 0; u < U; ++u) xv[u] = gather(x, c[u]);
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc = fma_acc(to_acc(v[u]), (TA)xv[u], acc);
-  }
-  for (; j < L; ++j) {
-    const IDX o = (IDX)j * (IDX)n_pad + (IDX)i;
-    const int32_t c = __ldcs(col + o);
-    const TV v = ld_stream1(val + o);
-    acc = fma_acc(to_acc(v), (TA)__ldg(x + c), acc);
+    for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? fma_acc(to_acc(v[u]), (TA)xv[u], acc) : acc;
   }
   y[i] = (TX)acc;
 }

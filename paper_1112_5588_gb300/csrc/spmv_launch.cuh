@@ -13,6 +13,7 @@ struct LaunchCfg {
   int rows_per_thread;  // R: 1, 2, 4
   int threads_per_row;  // T: 1, 2, 4, 8
   int block_threads;    // CTA size
+  int unroll;           // U: jagged diagonals per chunk of the j-loop
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -32,21 +33,36 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
   if (grid > 0x7fffffffLL) return set_error(PJDS_EOVERFLOW, "grid too large");
   const dim3 g((unsigned)grid), blk((unsigned)nt);
 #define PJDS_ARGS val, A->col, A->col_start, A->block_len, A->perm, x, y, A->n_rows, A->n_pad, A->b
-  if (T == 1) {
-    switch (R) {
-      case 1: dev::pjds_rows_kernel<TV, TX, IDX, 1, 8, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
-      case 2: dev::pjds_rows_kernel<TV, TX, IDX, 2, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
-      case 4: dev::pjds_rows_kernel<TV, TX, IDX, 4, 2, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
-      default: return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
-    }
+  const int U = c.unroll;
+#define PJDS_ROWS(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
+#define PJDS_TPR(TT, UU) dev::pjds_tpr_kernel<TV, TX, IDX, TT, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
+  if (T == 1 && R == 1) {
+    if (U == 4) PJDS_ROWS(1, 4);
+    else if (U == 8) PJDS_ROWS(1, 8);
+    else if (U == 16) PJDS_ROWS(1, 16);
+    else return set_error(PJDS_EINVAL, "unroll must be 4, 8 or 16 for one row per thread");
+  } else if (T == 1 && R == 2) {
+    if (U == 2) PJDS_ROWS(2, 2);
+    else if (U == 4) PJDS_ROWS(2, 4);
+    else if (U == 8) PJDS_ROWS(2, 8);
+    else return set_error(PJDS_EINVAL, "unroll must be 2, 4 or 8 for two rows per thread");
+  } else if (T == 1 && R == 4) {
+    if (U == 2) PJDS_ROWS(4, 2);
+    else if (U == 4) PJDS_ROWS(4, 4);
+    else return set_error(PJDS_EINVAL, "unroll must be 2 or 4 for four rows per thread");
+  } else if (T == 1) {
+    return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
   } else {
+    if (U != 2 && U != 4) return set_error(PJDS_EINVAL, "unroll must be 2 or 4 with threads_per_row > 1");
     switch (T) {
-      case 2: dev::pjds_tpr_kernel<TV, TX, IDX, 2, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
-      case 4: dev::pjds_tpr_kernel<TV, TX, IDX, 4, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
-      case 8: dev::pjds_tpr_kernel<TV, TX, IDX, 8, 4, SC><<<g, blk, 0, s>>>(PJDS_ARGS); break;
+      case 2: if (U == 2) PJDS_TPR(2, 2); else PJDS_TPR(2, 4); break;
+      case 4: if (U == 2) PJDS_TPR(4, 2); else PJDS_TPR(4, 4); break;
+      case 8: if (U == 2) PJDS_TPR(8, 2); else PJDS_TPR(8, 4); break;
       default: return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
     }
   }
+#undef PJDS_ROWS
+#undef PJDS_TPR
 #undef PJDS_ARGS
   return check_launch("pjds_spmv launch");
 }

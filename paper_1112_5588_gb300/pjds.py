@@ -52,7 +52,7 @@ class _PjdsDevS(ctypes.Structure):
 
 
 class _LaunchS(ctypes.Structure):
-    _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("reserved", _i32)]
+    _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32)]
 
 
 class _EllrHostS(ctypes.Structure):
@@ -253,11 +253,11 @@ def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> t
 
 
 def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
-                  threads_per_row: int = 0, block_threads: int = 0, stream=None) -> torch.Tensor:
+                  threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, stream=None) -> torch.Tensor:
     """y = A x with an explicit kernel configuration (pjds_spmv_cfg)."""
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, 0)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y

@@ -168,5 +168,8 @@ def test_spmv_argument_checks_without_gpu(P):
     assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
     cfg = P._LaunchS(1, 1, 1000, 0)
     assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
+    for bad in ((1, 1, 256, 3), (2, 1, 256, 16), (4, 1, 256, 8), (1, 2, 256, 8)):
+        cfg = P._LaunchS(*bad)
+        assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1, bad
     s.n_pad = 33
     assert lib.pjds_spmv(ctypes.byref(s), fake, fake, None) == -1

@@ -84,6 +84,8 @@ def test_pjds_fp64_matches_oracle(P, oracle_lib, name, make, b):
     dict(rows_per_thread=1, block_threads=128), dict(rows_per_thread=1, block_threads=512),
     dict(rows_per_thread=2), dict(rows_per_thread=4), dict(rows_per_thread=4, block_threads=64),
     dict(threads_per_row=2), dict(threads_per_row=4), dict(threads_per_row=8, block_threads=512),
+    dict(unroll=4), dict(unroll=16), dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=2, unroll=2),
+    dict(rows_per_thread=4, unroll=4), dict(threads_per_row=4, unroll=2), dict(threads_per_row=2, block_threads=32),
 ], ids=lambda c: "-".join(f"{k[0]}{v}" for k, v in c.items()))
 @pytest.mark.parametrize("name,make", [SHAPES[1], SHAPES[4], SHAPES[6]], ids=["ragged", "fullrow", "zipf"])
 def test_pjds_configs_match_oracle(P, oracle_lib, cfg, name, make):
@@ -100,9 +102,10 @@ def test_rows_per_thread_bit_identical_to_one_row(P):
     A = synth.zipf_rows(40_000, s=1.7, len_max=300, seed=9)
     x = synth.vector(A.n_cols, seed=9)
     y1, _, _ = run_pjds(P, A, x, cfg=dict(rows_per_thread=1))
-    for R in (2, 4):
-        yR, _, _ = run_pjds(P, A, x, cfg=dict(rows_per_thread=R))
-        assert np.array_equal(y1.view(np.uint64), yR.view(np.uint64))
+    for cfg in (dict(rows_per_thread=2), dict(rows_per_thread=4), dict(unroll=4), dict(unroll=16),
+                dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=4, unroll=4)):
+        yR, _, _ = run_pjds(P, A, x, cfg=cfg)
+        assert np.array_equal(y1.view(np.uint64), yR.view(np.uint64)), cfg
 
 
 @pytest.mark.parametrize("name,make", SHAPES[:6], ids=[s[0] for s in SHAPES[:6]])
