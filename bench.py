@@ -222,7 +222,7 @@ def run_ours(args, world, rank, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_1112_5588_gb300 import pjds
+    from paper_1112_5588_gb300 import pjds, replicas
 
     dist_on = world > 1
     if dist_on:
@@ -258,12 +258,9 @@ def run_ours(args, world, rank, local_rank):
         barrier()
         torch.cuda.synchronize()
     gpu_launches = args.steps
-    t_total = sum(durs)
-    if dist_on:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = nbytes * args.steps * world / t_total / 1e9
+    # replicas: units of all ranks over the slowest rank's time
+    total_bytes, t_total, rate = replicas.aggregate(nbytes * args.steps, sum(durs), dev if dist_on else None)
+    value = rate / 1e9
     per_launch = t_total / args.steps
     peak, peak_kind = hbm_peak()
     achieved = nbytes / (sum(durs) / len(durs)) / 1e9
@@ -286,12 +283,8 @@ def run_ours(args, world, rank, local_rank):
         t0 = time.perf_counter()
         pjds.pjds_spmv_host(D, xh, yh, xd, yd)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_t)
-    if dist_on:
-        tt = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
-    e2e_value = nbytes * args.steps * world / e2e_total / 1e9
+    _, _, e2e_rate = replicas.aggregate(nbytes * args.steps, sum(e2e_t), dev if dist_on else None)
+    e2e_value = e2e_rate / 1e9
 
     if rank != 0:
         if dist_on:
@@ -328,10 +321,10 @@ def run_ours(args, world, rank, local_rank):
         "config": {"workload": workload_desc(A.n_rows), "n_rows": A.n_rows, "nnz": A.nnz, "n_stored": n_stored,
                    "b": 32, "alg_bytes_per_step": nbytes, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU", "seed": args.seed},
-        "gflops": round(2 * A.nnz * args.steps * world / t_total / 1e9, 3),
+        "gflops": round(value * 2 * A.nnz / nbytes, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "pjds_rows_kernel<double,double,int,1,8,true>", "peak_kind": peak_kind},
+                     "kernel": "pjds_rows_kernel<double,double,int,R=1,U=4,scatter> 128 thr/CTA", "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": 8 * A.n_cols,
                 "d2h_bytes_per_step": 8 * A.n_rows},

@@ -40,8 +40,8 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   const int R = c.rows_per_thread, T = c.threads_per_row;
   if (R != 1 && R != 2 && R != 4) return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
   if (T != 1 && T != 2 && T != 4 && T != 8) return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
-  if (R > 1 && T > 1) return set_error(PJDS_EINVAL, "rows_per_thread > 1 needs threads_per_row = 1");
-  if (c.unroll == 0) c.unroll = R == 1 ? 8 : (R == 2 ? 4 : 2);
+  if (c.unroll == 0) c.unroll = T > 1 ? 4 : (R == 1 ? (A->dtype == PJDS_F32 ? 8 : 4) : (R == 2 ? 4 : 2));
+  if (c.unroll == 0) c.unroll = T > 1 ? 4 : (R == 1 ? 8 : (R == 2 ? 4 : 2));
   if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32)
     return set_error(PJDS_EINVAL, "block_threads must be a multiple of 32 in [32, 512]");
   if (R > 1) {
@@ -53,15 +53,17 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   return PJDS_OK;
 }
 
-// Default configuration: one thread per row (the paper's mapping), 256
-// threads per CTA.
+// Default configuration, from sweeps on GB300 (HMEp-like, stencil, Zipf and
+// DLR-like matrices): one thread per row (the paper's mapping) with 4 (fp64,
+// bf16) or 8 (fp32) jagged diagonals per load round; matrices whose longest
+// row has 64 or more entries use two threads per row. pjds_spmv_cfg
+// overrides any field.
 static LaunchCfg default_cfg(const pjds_dev *A) {
-  (void)A;
   LaunchCfg c;
   c.rows_per_thread = 1;
-  c.threads_per_row = 1;
-  c.block_threads = 256;
-  c.unroll = 0;
+  c.threads_per_row = A->n_max >= 64 ? 2 : 1;
+  c.block_threads = A->dtype == PJDS_F32 ? 256 : 128;
+  c.unroll = 0;  // filled in by check_cfg once R and T are final
   return c;
 }
 
@@ -85,8 +87,12 @@ extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pj
   if (rc) return rc;
   LaunchCfg c = default_cfg(A);
   if (cfg) {
+    // a field left at 0 keeps its default; asking for several rows per thread
+    // implies one thread per row and vice versa
     if (cfg->rows_per_thread) c.rows_per_thread = cfg->rows_per_thread;
     if (cfg->threads_per_row) c.threads_per_row = cfg->threads_per_row;
+    if (cfg->rows_per_thread > 1 && !cfg->threads_per_row) c.threads_per_row = 1;
+    if (cfg->threads_per_row > 1 && !cfg->rows_per_thread) c.rows_per_thread = 1;
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
     if (cfg->unroll) c.unroll = cfg->unroll;
   }
