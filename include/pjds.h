@@ -159,6 +159,15 @@ typedef struct pjds_launch {
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
 
 /*
+ * The configuration pjds_spmv_cfg would launch for A and cfg (cfg = NULL: the
+ * pjds_spmv default), with every 0 field replaced by its default, written to
+ * *out; nothing is launched and no device memory is touched. Fields left at 0
+ * take defaults; rows_per_thread > 1 alone implies threads_per_row = 1 and
+ * vice versa. Returns PJDS_EINVAL for a combination pjds_spmv_cfg rejects.
+ */
+int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *out);
+
+/*
  * End-to-end product from host memory: copies x_host (n_cols elements) into
  * the caller's device buffer x_dev, runs pjds_spmv into y_dev, copies y_dev
  * back into y_host (n_rows elements) and waits for the stream. Host buffers

@@ -7,14 +7,14 @@
 
 namespace pjds {
 
-static int check_pjds_dev(const pjds_dev *A, const void *x, const void *y) {
+static int check_pjds_dev(const pjds_dev *A, const void *x, const void *y, bool need_vectors = true) {
   if (!A) return set_error(PJDS_EINVAL, "A is NULL");
   if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "unknown dtype %d", A->dtype);
   if (A->n_rows < 0 || A->n_cols < 1 || A->b <= 0 || A->b % 32 != 0)
     return set_error(PJDS_EINVAL, "bad sizes (n_rows %d, n_cols %d, b %d)", A->n_rows, A->n_cols, A->b);
   if ((int64_t)A->n_pad != ((int64_t)A->n_rows + A->b - 1) / A->b * A->b || A->n_blocks != A->n_pad / A->b)
     return set_error(PJDS_EINVAL, "n_pad/n_blocks inconsistent with n_rows and b");
-  if (A->n_rows > 0 && (!x || !y)) return set_error(PJDS_EINVAL, "x or y is NULL");
+  if (need_vectors && A->n_rows > 0 && (!x || !y)) return set_error(PJDS_EINVAL, "x or y is NULL");
   if (A->n_stored > 0 && (!A->val || !A->col || !A->col_start || !A->block_len))
     return set_error(PJDS_EINVAL, "a matrix array is NULL");
   if (A->n_rows > 0 && !A->permute_cols && !A->perm) return set_error(PJDS_EINVAL, "perm is NULL");
@@ -40,8 +40,12 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   const int R = c.rows_per_thread, T = c.threads_per_row;
   if (R != 1 && R != 2 && R != 4) return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
   if (T != 1 && T != 2 && T != 4 && T != 8) return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
+  if (R > 1 && T > 1) return set_error(PJDS_EINVAL, "rows_per_thread > 1 needs threads_per_row = 1");
   if (c.unroll == 0) c.unroll = T > 1 ? 4 : (R == 1 ? (A->dtype == PJDS_F32 ? 8 : 4) : (R == 2 ? 4 : 2));
-  if (c.unroll == 0) c.unroll = T > 1 ? 4 : (R == 1 ? 8 : (R == 2 ? 4 : 2));
+  const int U = c.unroll;
+  const bool u_ok = T > 1 ? (U == 2 || U == 4)
+                          : R == 1 ? (U == 4 || U == 8 || U == 16) : R == 2 ? (U == 2 || U == 4 || U == 8) : (U == 2 || U == 4);
+  if (!u_ok) return set_error(PJDS_EINVAL, "unroll %d is not available for rows_per_thread %d, threads_per_row %d", U, R, T);
   if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32)
     return set_error(PJDS_EINVAL, "block_threads must be a multiple of 32 in [32, 512]");
   if (R > 1) {
@@ -81,11 +85,8 @@ extern "C" int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream) {
-  clear_error();
-  int rc = check_pjds_dev(A, x, y);
-  if (rc) return rc;
-  LaunchCfg c = default_cfg(A);
+static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) {
+  c = default_cfg(A);
   if (cfg) {
     // a field left at 0 keeps its default; asking for several rows per thread
     // implies one thread per row and vice versa
@@ -96,7 +97,30 @@ extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pj
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
     if (cfg->unroll) c.unroll = cfg->unroll;
   }
-  rc = check_cfg(A, c);
+  return check_cfg(A, c);
+}
+
+extern "C" int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *out) {
+  clear_error();
+  if (!A || !out) return set_error(PJDS_EINVAL, "A or out is NULL");
+  int rc = check_pjds_dev(A, nullptr, nullptr, false);
+  if (rc) return rc;
+  LaunchCfg c;
+  rc = resolve_cfg(A, cfg, c);
+  if (rc) return rc;
+  out->rows_per_thread = c.rows_per_thread;
+  out->threads_per_row = c.threads_per_row;
+  out->block_threads = c.block_threads;
+  out->unroll = c.unroll;
+  return PJDS_OK;
+}
+
+extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream) {
+  clear_error();
+  int rc = check_pjds_dev(A, x, y);
+  if (rc) return rc;
+  LaunchCfg c;
+  rc = resolve_cfg(A, cfg, c);
   if (rc) return rc;
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
 }

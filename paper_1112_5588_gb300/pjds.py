@@ -81,6 +81,7 @@ def _load_lib():
         "pjds_spmv": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_spmv_cfg": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, P(_LaunchS), _vp]),
         "pjds_spmv_host": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp, _vp, _vp]),
+        "pjds_spmv_resolve": (ctypes.c_int, [P(_PjdsDevS), P(_LaunchS), P(_LaunchS)]),
         "pjds_permute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_unpermute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "ellr_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, P(P(_EllrHostS))]),
@@ -261,6 +262,27 @@ def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thre
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y
+
+
+def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, block_threads: int = 0,
+                      unroll: int = 0) -> dict:
+    """The launch configuration pjds_spmv_cfg would use (no launch). `A` is a
+    PjdsDevice or a PjdsHost (only sizes and alignment are read)."""
+    s = A.struct if isinstance(A, PjdsDevice) else _dev_struct_from_host(A)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll)
+    out = _LaunchS()
+    _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
+    return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
+            "block_threads": out.block_threads, "unroll": out.unroll}
+
+
+def _dev_struct_from_host(H: "PjdsHost"):
+    s = _PjdsDevS()
+    for f, _ in _PjdsDevS._fields_[:10]:
+        setattr(s, f, getattr(H, f))
+    # alignment of torch allocations (512 B) stands in for the device pointers
+    s.val = s.col = s.col_start = s.block_len = s.perm = 512
+    return s
 
 
 def pjds_spmv_host(A: PjdsDevice, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor,

@@ -153,23 +153,48 @@ def test_error_paths_return_status(P):
 
 
 def test_spmv_argument_checks_without_gpu(P):
-    # Invalid configurations are rejected on the host before any launch.
+    # Invalid configurations and inconsistent matrix views are rejected on the
+    # host; pjds_spmv_resolve runs the same checks as pjds_spmv_cfg but never
+    # launches, so no fake pointer can reach a kernel.
     A = tiny.random_lengths(64, 64, max_len=8, seed=1)
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
-    s = P._PjdsDevS()
-    for f, _ in P._PjdsDevS._fields_[:10]:
-        setattr(s, f, getattr(H, f))
-    lib = P.lib()
-    cfg = P._LaunchS(3, 1, 256, 0)
-    fake = ctypes.c_void_p(16)
-    s.val = s.col = s.col_start = s.block_len = s.perm = 256
-    assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
-    cfg = P._LaunchS(2, 2, 256, 0)
-    assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
-    cfg = P._LaunchS(1, 1, 1000, 0)
-    assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1
-    for bad in ((1, 1, 256, 3), (2, 1, 256, 16), (4, 1, 256, 8), (1, 2, 256, 8)):
-        cfg = P._LaunchS(*bad)
-        assert lib.pjds_spmv_cfg(ctypes.byref(s), fake, fake, ctypes.byref(cfg), None) == -1, bad
+    for bad in (dict(rows_per_thread=3), dict(rows_per_thread=2, threads_per_row=2),
+                dict(block_threads=1000), dict(block_threads=48), dict(threads_per_row=1, unroll=3),
+                dict(rows_per_thread=2, unroll=16), dict(rows_per_thread=4, unroll=8),
+                dict(threads_per_row=2, unroll=8)):
+        with pytest.raises(P.PjdsError) as ei:
+            P.pjds_spmv_resolve(H, **bad)
+        assert ei.value.code == -1, bad
+    s = P._dev_struct_from_host(H)
     s.n_pad = 33
-    assert lib.pjds_spmv(ctypes.byref(s), fake, fake, None) == -1
+    out = P._LaunchS()
+    assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(out)) == -1
+    s = P._dev_struct_from_host(H)
+    s.val = 8  # misaligned for 4-row vector loads
+    cfg = P._LaunchS(4, 1, 256, 0)
+    assert P.lib().pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)) == -1
+    assert P.lib().pjds_spmv(None, None, None, None) == -1
+
+
+def test_gpu_test_configs_resolve_on_host(P):
+    # every configuration the GPU tests launch is accepted by the library
+    from tests.test_gpu_spmv import CONFIG_SHAPES, CONFIGS
+    for _, make in CONFIG_SHAPES:
+        A = make()
+        H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+        for cfg in CONFIGS:
+            r = P.pjds_spmv_resolve(H, **cfg)
+            assert all(r[k] == v for k, v in cfg.items()), (cfg, r)
+        assert P.pjds_spmv_resolve(H)["unroll"] in (4, 8)
+
+
+def test_resolve_defaults(P):
+    A = synth.hmep_like(n=10_000, seed=1)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128, "unroll": 4}
+    Z = synth.zipf_rows(10_000, s=2.0, len_max=512, seed=1)
+    HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
+    assert P.pjds_spmv_resolve(HZ)["threads_per_row"] == 2
+    assert P.pjds_spmv_resolve(HZ, rows_per_thread=2)["threads_per_row"] == 1
+    with pytest.raises(P.PjdsError):
+        P.pjds_spmv_resolve(HZ, unroll=16)

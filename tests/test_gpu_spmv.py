@@ -69,6 +69,16 @@ SHAPES = [
 ]
 
 
+CONFIGS = [
+    dict(rows_per_thread=1, block_threads=128), dict(rows_per_thread=1, block_threads=512),
+    dict(rows_per_thread=2), dict(rows_per_thread=4), dict(rows_per_thread=4, block_threads=64),
+    dict(threads_per_row=2), dict(threads_per_row=4), dict(threads_per_row=8, block_threads=512),
+    dict(threads_per_row=1, unroll=4), dict(threads_per_row=1, unroll=16), dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=2, unroll=2),
+    dict(rows_per_thread=4, unroll=4), dict(threads_per_row=4, unroll=2), dict(threads_per_row=2, block_threads=32),
+]
+CONFIG_SHAPES = [SHAPES[1], SHAPES[4], SHAPES[6]]
+
+
 @pytest.mark.parametrize("name,make", SHAPES, ids=[s[0] for s in SHAPES])
 @pytest.mark.parametrize("b", [32, 128])
 def test_pjds_fp64_matches_oracle(P, oracle_lib, name, make, b):
@@ -80,14 +90,8 @@ def test_pjds_fp64_matches_oracle(P, oracle_lib, name, make, b):
     assert r["ok"], r
 
 
-@pytest.mark.parametrize("cfg", [
-    dict(rows_per_thread=1, block_threads=128), dict(rows_per_thread=1, block_threads=512),
-    dict(rows_per_thread=2), dict(rows_per_thread=4), dict(rows_per_thread=4, block_threads=64),
-    dict(threads_per_row=2), dict(threads_per_row=4), dict(threads_per_row=8, block_threads=512),
-    dict(unroll=4), dict(unroll=16), dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=2, unroll=2),
-    dict(rows_per_thread=4, unroll=4), dict(threads_per_row=4, unroll=2), dict(threads_per_row=2, block_threads=32),
-], ids=lambda c: "-".join(f"{k[0]}{v}" for k, v in c.items()))
-@pytest.mark.parametrize("name,make", [SHAPES[1], SHAPES[4], SHAPES[6]], ids=["ragged", "fullrow", "zipf"])
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "-".join(f"{k[0]}{v}" for k, v in c.items()))
+@pytest.mark.parametrize("name,make", CONFIG_SHAPES, ids=["ragged", "fullrow", "zipf"])
 def test_pjds_configs_match_oracle(P, oracle_lib, cfg, name, make):
     A = make()
     x = synth.vector(A.n_cols, seed=12)
@@ -101,8 +105,9 @@ def test_rows_per_thread_bit_identical_to_one_row(P):
     # R rows per thread only changes the load width, not any row's arithmetic.
     A = synth.zipf_rows(40_000, s=1.7, len_max=300, seed=9)
     x = synth.vector(A.n_cols, seed=9)
-    y1, _, _ = run_pjds(P, A, x, cfg=dict(rows_per_thread=1))
-    for cfg in (dict(rows_per_thread=2), dict(rows_per_thread=4), dict(unroll=4), dict(unroll=16),
+    y1, _, _ = run_pjds(P, A, x, cfg=dict(rows_per_thread=1, threads_per_row=1))
+    for cfg in (dict(rows_per_thread=2), dict(rows_per_thread=4), dict(threads_per_row=1, unroll=8),
+                dict(threads_per_row=1, unroll=16),
                 dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=4, unroll=4)):
         yR, _, _ = run_pjds(P, A, x, cfg=cfg)
         assert np.array_equal(y1.view(np.uint64), yR.view(np.uint64)), cfg
