@@ -44,7 +44,10 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the timed pJDS kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload; valid only
 # while the kernel sources hash to the recorded value.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/pjds_rows_kernel_hmep6.2M_f64.md: 1.62 GB read + 161 MB write per launch
+    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_781_000_000, "src": "bc3cf561b6fbec2a"},
+}
 
 
 def kernel_source_hash() -> str:

@@ -121,8 +121,8 @@ def test_ellr_fp64_matches_oracle_and_pjds_bitwise(P, oracle_lib, name, make):
     y_ref, absax, lens = oracle_ref(oracle_lib, A, x)
     r = parity.check_fp64(ye, y_ref, absax, lens)
     assert r["ok"], r
-    # same per-row order and fused multiply-add in both kernels
-    yp, _, _ = run_pjds(P, A, x)
+    # same per-row order and fused multiply-add in both kernels (one thread per row)
+    yp, _, _ = run_pjds(P, A, x, cfg=dict(threads_per_row=1))
     assert np.array_equal(ye.view(np.uint64), yp.view(np.uint64))
 
 
@@ -169,7 +169,7 @@ def test_reduced_precision_matches_oracle(P, oracle_lib, dtype, name, make):
     A = make()
     x32 = synth.vector(A.n_cols, seed=14).astype(np.float32)
     xd = x32.astype(np.float64)
-    y, _, _ = run_pjds(P, A, x32, dtype=dtype)
+    y, _, _ = run_pjds(P, A, x32, dtype=dtype, cfg=dict(threads_per_row=1))
     Ar = A._replace(val=oracle_lib.round_f32(A.val) if dtype == "f32" else oracle_lib.round_bf16(A.val))
     y_ref, absax, lens = oracle_ref(oracle_lib, Ar, xd)
     r = parity.check_fp32(y, y_ref, absax, lens)
