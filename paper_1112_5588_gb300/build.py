@@ -32,8 +32,8 @@ def _nvcc() -> str:
 
 
 def _deps() -> list:
-    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [
-        os.path.join(INCLUDE, "pjds.h")]
+    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(
+        os.path.join(INCLUDE, "*.h"))
 
 
 def _stale(src: str, obj: str, deps: list) -> bool:

@@ -1,0 +1,722 @@
+// Krylov drivers on pJDS matrices in the permuted basis (include/pjds_krylov.h):
+// mixed-precision CG with fp64 residual refinement, Lanczos, fp64 Ritz refine.
+//
+// Every step runs in the kernels below; the host only sequences launches,
+// reads one residual norm per outer CG step and solves the small tridiagonal
+// eigenproblem. Scalars (alpha, beta, norms) live in device memory and are
+// read by the kernels that need them, so a run of inner iterations has no
+// host round trip and can be captured once in a CUDA graph. Inner products
+// accumulate in fp64 with a fixed reduction order: per-CTA partial sums
+// (warp shuffles, then one warp) into the workspace, then one CTA adds the
+// partials in a fixed pattern — results are bitwise reproducible.
+#include <float.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.h"
+#include "pjds_krylov.h"
+#include "spmv_kernels.cuh"
+
+namespace pjds {
+namespace kry {
+
+constexpr int KT = 256;      // threads per CTA of the vector and product kernels
+constexpr int FIN_T = 1024;  // threads of the one-CTA finalisation
+
+// slots of the device scalar block
+enum { S_RR = 0, S_PQ, S_ALPHA, S_BETA, S_NRM, S_INVNRM, S_AUX0, S_AUX1, S_AUX2, S_COUNT = 16 };
+// finalisation operations
+enum { F_ALPHA = 0, F_BETA, F_RR, F_NORM, F_LALPHA, F_LBETA, F_STORE };
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[KT / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = l < KT / 32 ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;  // complete in thread 0
+}
+
+// One sorted row's product in the permuted basis (Listing 2 with the loop
+// bound of the row's block; pads carry column -1 and are skipped).
+template <typename TV, typename TX, typename IDX>
+__device__ __forceinline__ typename dev::Acc<TV>::T row_product(const TV *__restrict__ val,
+                                                                 const int32_t *__restrict__ col,
+                                                                 const int64_t *__restrict__ col_start, int32_t L,
+                                                                 int64_t i, const TX *__restrict__ x) {
+  using TA = typename dev::Acc<TV>::T;
+  constexpr int U = 4;
+  TA acc = TA(0);
+  for (int32_t j = 0; j < L; j += U) {
+    int32_t c[U];
+    TV v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < L) {
+        const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i;
+        c[u] = __ldcs(col + o);
+        v[u] = dev::ld_stream1(val + o);
+      } else {
+        c[u] = -1;
+        v[u] = TV{};
+      }
+    }
+    TX xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = dev::gather(x, c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
+  }
+  return acc;
+}
+
+// MODE 0: y = A x and partial = sum x_i y_i.  MODE 1: y = bv - A x and
+// partial = sum y_i^2 (the fp64 residual of the refinement loop).
+template <typename TV, typename TX, typename IDX, int MODE>
+__global__ void __launch_bounds__(KT)
+    spmv_dot_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ col_start,
+                    const int32_t *__restrict__ block_len, const TX *__restrict__ x, TX *__restrict__ y,
+                    const TX *__restrict__ bv, double *__restrict__ partial, int32_t n_rows, int32_t b) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  double contrib = 0.0;
+  if (i < n_rows) {
+    const int32_t L = __ldg(block_len + (int32_t)(i / b));
+    const auto acc = row_product<TV, TX, IDX>(val, col, col_start, L, i, x);
+    TX yi;
+    if constexpr (MODE == 0) {
+      yi = (TX)acc;
+      contrib = (double)x[i] * (double)yi;
+    } else {
+      yi = (TX)((double)bv[i] - (double)acc);
+      contrib = (double)yi * (double)yi;
+    }
+    y[i] = yi;
+  }
+  const double s = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// Fixed-order sum of nb partials, then the scalar update `op`.
+__global__ void __launch_bounds__(FIN_T)
+    finalize_kernel(const double *__restrict__ partial, int32_t nb, double *__restrict__ scal, int32_t op,
+                    double *__restrict__ out, int32_t j) {
+  __shared__ double sh[FIN_T / 32];
+  double v = 0.0;
+  for (int32_t k = threadIdx.x; k < nb; k += FIN_T) v += partial[k];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w != 0) return;
+  v = l < FIN_T / 32 ? sh[l] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (l != 0) return;
+  switch (op) {
+    case F_ALPHA:  // alpha = (r, r) / (p, A p)
+      scal[S_PQ] = v;
+      scal[S_ALPHA] = v != 0.0 ? scal[S_RR] / v : 0.0;
+      break;
+    case F_BETA:  // beta = (r', r') / (r, r)
+      scal[S_BETA] = scal[S_RR] != 0.0 ? v / scal[S_RR] : 0.0;
+      scal[S_RR] = v;
+      break;
+    case F_RR:
+      scal[S_RR] = v;
+      break;
+    case F_NORM: {
+      const double nrm = sqrt(v);
+      scal[S_NRM] = nrm;
+      scal[S_INVNRM] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      break;
+    }
+    case F_LALPHA:
+      out[j] = v;
+      break;
+    case F_LBETA: {
+      const double nrm = sqrt(v);
+      out[j] = nrm;
+      scal[S_INVNRM] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      break;
+    }
+    default:  // F_STORE
+      scal[j] = v;
+      break;
+  }
+}
+
+template <typename TX>
+__global__ void __launch_bounds__(KT) sumsq_kernel(const TX *__restrict__ v, double *__restrict__ partial, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  const double x = i < n ? (double)v[i] : 0.0;
+  const double s = block_sum(x * x);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// d += alpha p; r -= alpha q; partial = sum r_i^2
+template <typename TX>
+__global__ void __launch_bounds__(KT)
+    cg_update_kernel(TX *__restrict__ d, TX *__restrict__ r, const TX *__restrict__ p, const TX *__restrict__ q,
+                     const double *__restrict__ scal, double *__restrict__ partial, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  double contrib = 0.0;
+  if (i < n) {
+    const TX a = (TX)scal[S_ALPHA];
+    d[i] = d[i] + a * p[i];
+    const TX ri = r[i] - a * q[i];
+    r[i] = ri;
+    contrib = (double)ri * (double)ri;
+  }
+  const double s = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// p = r + beta p
+template <typename TX>
+__global__ void __launch_bounds__(KT)
+    cg_dir_kernel(TX *__restrict__ p, const TX *__restrict__ r, const double *__restrict__ scal, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  if (i < n) p[i] = r[i] + (TX)scal[S_BETA] * p[i];
+}
+
+// Start of an inner solve: r = p = (r64 / ||r64||) in the inner type, d = 0,
+// partial = sum r_i^2.
+template <typename TL>
+__global__ void __launch_bounds__(KT)
+    ir_start_kernel(const double *__restrict__ r64, TL *__restrict__ r, TL *__restrict__ p, TL *__restrict__ d,
+                    const double *__restrict__ scal, double *__restrict__ partial, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  double contrib = 0.0;
+  if (i < n) {
+    const TL ri = (TL)(r64[i] * scal[S_INVNRM]);
+    r[i] = ri;
+    p[i] = ri;
+    d[i] = TL(0);
+    contrib = (double)ri * (double)ri;
+  }
+  const double s = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// x += ||r64|| d (fp64)
+template <typename TL>
+__global__ void __launch_bounds__(KT)
+    ir_correct_kernel(double *__restrict__ x, const TL *__restrict__ d, const double *__restrict__ scal, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  if (i < n) x[i] = fma(scal[S_NRM], (double)d[i], x[i]);
+}
+
+// v = v0 / ||v0||, vprev = 0
+template <typename TX>
+__global__ void __launch_bounds__(KT)
+    lanczos_start_kernel(const TX *__restrict__ v0, TX *__restrict__ v, TX *__restrict__ vprev,
+                         const double *__restrict__ scal, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  if (i < n) {
+    v[i] = (TX)((double)v0[i] * scal[S_INVNRM]);
+    vprev[i] = TX(0);
+  }
+}
+
+// w = w - alpha_j v - beta_j vprev (in fp64, stored in TX); partial = sum w_i^2
+template <typename TX>
+__global__ void __launch_bounds__(KT)
+    lanczos_orth_kernel(TX *__restrict__ w, const TX *__restrict__ v, const TX *__restrict__ vprev,
+                        const double *__restrict__ alpha, const double *__restrict__ beta, int32_t j,
+                        double *__restrict__ partial, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  double contrib = 0.0;
+  if (i < n) {
+    const double wi = (double)w[i] - alpha[j] * (double)v[i] - beta[j] * (double)vprev[i];
+    const TX ws = (TX)wi;
+    w[i] = ws;
+    contrib = (double)ws * (double)ws;
+  }
+  const double s = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// basis_row = v (optional); vprev = v; v = w / beta_{j+1}
+template <typename TX>
+__global__ void __launch_bounds__(KT)
+    lanczos_next_kernel(TX *__restrict__ vprev, TX *__restrict__ v, const TX *__restrict__ w,
+                        const double *__restrict__ scal, TX *__restrict__ basis_row, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  if (i < n) {
+    const TX vi = v[i];
+    if (basis_row) basis_row[i] = vi;
+    vprev[i] = vi;
+    v[i] = (TX)((double)w[i] * scal[S_INVNRM]);
+  }
+}
+
+// y = sum_j s_j basis[j] (fp64); partial = sum y_i^2
+template <typename TB>
+__global__ void __launch_bounds__(KT)
+    ritz_combine_kernel(const TB *__restrict__ basis, const double *__restrict__ s, int32_t k, int32_t n,
+                        double *__restrict__ y, double *__restrict__ partial) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  double contrib = 0.0;
+  if (i < n) {
+    double acc = 0.0;
+    for (int32_t j = 0; j < k; ++j) acc = fma(s[j], (double)__ldcs(basis + (int64_t)j * n + i), acc);
+    y[i] = acc;
+    contrib = acc * acc;
+  }
+  const double sm = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm;
+}
+
+// partial = sum (w_i - theta y_i)^2 with theta = scal[S_AUX1] / scal[S_AUX0]
+__global__ void __launch_bounds__(KT)
+    ritz_residual_kernel(const double *__restrict__ w, const double *__restrict__ y, const double *__restrict__ scal,
+                         double *__restrict__ partial, int32_t n) {
+  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  double contrib = 0.0;
+  if (i < n) {
+    const double theta = scal[S_AUX1] / scal[S_AUX0];
+    const double e = w[i] - theta * y[i];
+    contrib = e * e;
+  }
+  const double s = block_sum(contrib);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// ----------------------------------------------------------------------------- host helpers
+
+static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+static inline int32_t n_blocks_of(int32_t n) { return (int32_t)(((int64_t)n + KT - 1) / KT); }
+
+struct Carve {
+  char *base;
+  size_t off, cap;
+  template <typename T>
+  T *take(size_t count) {
+    T *p = reinterpret_cast<T *>(base + off);
+    off += align256(count * sizeof(T));
+    return p;
+  }
+};
+
+static int launch_check(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static int check_square_permuted(const pjds_dev *A, const char *name) {
+  if (!A) return set_error(PJDS_EINVAL, "%s is NULL", name);
+  if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "%s: unknown dtype", name);
+  if (!A->permute_cols || A->n_rows != A->n_cols)
+    return set_error(PJDS_EINVAL, "%s must be square and created with permute_cols = 1", name);
+  if (A->b <= 0 || A->b % 32 || (int64_t)A->n_pad != ((int64_t)A->n_rows + A->b - 1) / A->b * A->b)
+    return set_error(PJDS_EINVAL, "%s: inconsistent n_pad / b", name);
+  if (A->n_stored > 0 && (!A->val || !A->col || !A->col_start || !A->block_len))
+    return set_error(PJDS_EINVAL, "%s: a matrix array is NULL", name);
+  return PJDS_OK;
+}
+
+// product kernels dispatched on value type and index width
+template <typename TV, typename TX, int MODE>
+static void launch_spmv_dot(const pjds_dev *A, const TX *x, TX *y, const TX *bv, double *partial, cudaStream_t s) {
+  const int32_t nb = n_blocks_of(A->n_rows);
+  const TV *val = static_cast<const TV *>(A->val);
+  if (A->n_stored + A->n_pad < 0x7fffffffLL)
+    spmv_dot_kernel<TV, TX, int32_t, MODE>
+        <<<nb, KT, 0, s>>>(val, A->col, A->col_start, A->block_len, x, y, bv, partial, A->n_rows, A->b);
+  else
+    spmv_dot_kernel<TV, TX, int64_t, MODE>
+        <<<nb, KT, 0, s>>>(val, A->col, A->col_start, A->block_len, x, y, bv, partial, A->n_rows, A->b);
+}
+
+template <typename TX>
+static void spmv_dot_any(const pjds_dev *A, const TX *x, TX *y, double *partial, cudaStream_t s);
+template <>
+void spmv_dot_any<double>(const pjds_dev *A, const double *x, double *y, double *partial, cudaStream_t s) {
+  launch_spmv_dot<double, double, 0>(A, x, y, nullptr, partial, s);
+}
+template <>
+void spmv_dot_any<float>(const pjds_dev *A, const float *x, float *y, double *partial, cudaStream_t s) {
+  if (A->dtype == PJDS_BF16)
+    launch_spmv_dot<dev::bf16_t, float, 0>(A, x, y, nullptr, partial, s);
+  else
+    launch_spmv_dot<float, float, 0>(A, x, y, nullptr, partial, s);
+}
+
+static void finalize(double *partial, int32_t nb, double *scal, int op, double *out, int32_t j, cudaStream_t s) {
+  finalize_kernel<<<1, FIN_T, 0, s>>>(partial, nb, scal, op, out, j);
+}
+
+// ----------------------------------------------------------------------------- CG
+
+static size_t cg_bytes(int32_t n, int vec_bytes) {
+  return align256((size_t)n_blocks_of(n) * 8) + align256(S_COUNT * 8) + 4 * align256((size_t)n * vec_bytes) +
+         align256((size_t)n * 8);
+}
+
+template <typename TL>
+static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, double *x, const pjds_cg_opts &o,
+                  pjds_cg_result *res, void *work, cudaStream_t s) {
+  const int32_t n = Ah->n_rows, nb = n_blocks_of(n);
+  Carve cv{static_cast<char *>(work), 0, 0};
+  double *partial = cv.take<double>((size_t)nb);
+  double *scal = cv.take<double>(S_COUNT);
+  TL *r = cv.take<TL>((size_t)n), *p = cv.take<TL>((size_t)n), *q = cv.take<TL>((size_t)n);
+  TL *d = cv.take<TL>((size_t)n);
+  double *r64 = cv.take<double>((size_t)n);
+  int rc;
+
+  // ||b||
+  sumsq_kernel<double><<<nb, KT, 0, s>>>(b, partial, n);
+  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX2, s);
+  double bn2 = 0.0;
+  if ((rc = launch_check("cg ||b||"))) return rc;
+  cudaError_t e = cudaMemcpyAsync(&bn2, scal + S_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg: %s", cudaGetErrorString(e));
+  const double bnorm = sqrt(bn2);
+
+  auto inner_step = [&]() {
+    spmv_dot_any<TL>(Al, p, q, partial, s);                              // q = A p, (p, q)
+    finalize(partial, nb, scal, F_ALPHA, nullptr, 0, s);                 // alpha
+    cg_update_kernel<TL><<<nb, KT, 0, s>>>(d, r, p, q, scal, partial, n);  // d, r, (r, r)
+    finalize(partial, nb, scal, F_BETA, nullptr, 0, s);                  // beta
+    cg_dir_kernel<TL><<<nb, KT, 0, s>>>(p, r, scal, n);                  // p
+  };
+
+  cudaGraphExec_t exec = nullptr;
+  if (o.use_graph) {
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg graph capture: %s", cudaGetErrorString(e));
+    for (int it = 0; it < o.inner_iters; ++it) inner_step();
+    e = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg graph: %s", cudaGetErrorString(e));
+  }
+
+  pjds_cg_result out;
+  memset(&out, 0, sizeof(out));
+  double rel = 0.0;
+  rc = PJDS_OK;
+  for (int outer = 0;; ++outer) {
+    launch_spmv_dot<double, double, 1>(Ah, x, r64, b, partial, s);  // r64 = b - A x
+    finalize(partial, nb, scal, F_NORM, nullptr, 0, s);
+    if ((rc = launch_check("cg residual"))) break;
+    double rn = 0.0;
+    e = cudaMemcpyAsync(&rn, scal + S_NRM, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      rc = set_error(PJDS_ECUDA, "cg: %s", cudaGetErrorString(e));
+      break;
+    }
+    rel = bnorm > 0.0 ? rn / bnorm : rn;
+    if (out.n_history < PJDS_CG_HISTORY) out.history[out.n_history++] = rel;
+    if (outer >= o.max_outer || rel <= o.tol || rn == 0.0) break;
+    ir_start_kernel<TL><<<nb, KT, 0, s>>>(r64, r, p, d, scal, partial, n);
+    finalize(partial, nb, scal, F_RR, nullptr, 0, s);
+    if (exec) {
+      e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) {
+        rc = set_error(PJDS_ECUDA, "cg graph launch: %s", cudaGetErrorString(e));
+        break;
+      }
+    } else {
+      for (int it = 0; it < o.inner_iters; ++it) inner_step();
+    }
+    ir_correct_kernel<TL><<<nb, KT, 0, s>>>(x, d, scal, n);
+    if ((rc = launch_check("cg inner"))) break;
+    out.outer = outer + 1;
+    out.inner_total += o.inner_iters;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  out.rel_residual = rel;
+  if (res) *res = out;
+  return rc;
+}
+
+}  // namespace kry
+}  // namespace pjds
+
+using namespace pjds;
+using namespace pjds::kry;
+
+extern "C" int pjds_cg_workspace_bytes(int32_t n_rows, int32_t n_pad, int32_t vec_dtype, size_t *bytes) {
+  clear_error();
+  if (!bytes || n_rows < 0 || n_pad < n_rows) return set_error(PJDS_EINVAL, "bad arguments");
+  *bytes = cg_bytes(n_rows, vec_dtype == PJDS_F64 ? 8 : 4);
+  return PJDS_OK;
+}
+
+extern "C" int pjds_cg_solve(const pjds_dev *A_hi, const pjds_dev *A_lo, const double *b, double *x,
+                             const pjds_cg_opts *opts, pjds_cg_result *res, void *work, size_t work_bytes,
+                             void *stream) {
+  clear_error();
+  int rc = check_square_permuted(A_hi, "A_hi");
+  if (rc) return rc;
+  if (A_hi->dtype != PJDS_F64) return set_error(PJDS_EINVAL, "A_hi must hold fp64 values");
+  if (!A_lo) A_lo = A_hi;
+  if ((rc = check_square_permuted(A_lo, "A_lo"))) return rc;
+  if (A_lo->n_rows != A_hi->n_rows) return set_error(PJDS_EINVAL, "A_lo and A_hi differ in size");
+  if (A_hi->n_rows == 0) return PJDS_OK;
+  if (!b || !x || !work) return set_error(PJDS_EINVAL, "b, x or work is NULL");
+  pjds_cg_opts o{6, 50, 0.0, 1, 0};
+  if (opts) {
+    o = *opts;
+    if (o.max_outer <= 0) o.max_outer = 6;
+    if (o.inner_iters <= 0) o.inner_iters = 50;
+  }
+  if (o.inner_iters > 100000 || o.max_outer > 100000) return set_error(PJDS_EINVAL, "iteration counts too large");
+  const bool low = A_lo->dtype != PJDS_F64;
+  const size_t need = cg_bytes(A_hi->n_rows, low ? 4 : 8);
+  if (work_bytes < need) return set_error(PJDS_EINVAL, "workspace of %zu bytes is smaller than %zu", work_bytes, need);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return low ? cg_run<float>(A_hi, A_lo, b, x, o, res, work, s) : cg_run<double>(A_hi, A_lo, b, x, o, res, work, s);
+}
+
+// ----------------------------------------------------------------------------- Lanczos
+
+static size_t lanczos_bytes(int32_t n, int vec_bytes, int32_t steps) {
+  return align256((size_t)n_blocks_of(n) * 8) + align256(S_COUNT * 8) + align256((size_t)steps * 8) +
+         align256((size_t)(steps + 1) * 8) + 3 * align256((size_t)n * vec_bytes);
+}
+
+template <typename TX>
+static int lanczos_run(const pjds_dev *A, const TX *v0, int32_t steps, double *alpha_h, double *beta_h, TX *basis,
+                       int use_graph, void *work, cudaStream_t s) {
+  const int32_t n = A->n_rows, nb = n_blocks_of(n);
+  Carve cv{static_cast<char *>(work), 0, 0};
+  double *partial = cv.take<double>((size_t)nb);
+  double *scal = cv.take<double>(S_COUNT);
+  double *alpha = cv.take<double>((size_t)steps);
+  double *beta = cv.take<double>((size_t)steps + 1);
+  TX *v = cv.take<TX>((size_t)n), *vp = cv.take<TX>((size_t)n), *w = cv.take<TX>((size_t)n);
+  cudaError_t e = cudaMemsetAsync(beta, 0, sizeof(double) * ((size_t)steps + 1), s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos: %s", cudaGetErrorString(e));
+  sumsq_kernel<TX><<<nb, KT, 0, s>>>(v0, partial, n);
+  finalize(partial, nb, scal, F_NORM, nullptr, 0, s);
+  lanczos_start_kernel<TX><<<nb, KT, 0, s>>>(v0, v, vp, scal, n);
+  int rc = launch_check("lanczos start");
+  if (rc) return rc;
+  auto step = [&](int32_t j) {
+    spmv_dot_any<TX>(A, v, w, partial, s);  // w = A v, (v, w)
+    finalize(partial, nb, scal, F_LALPHA, alpha, j, s);
+    lanczos_orth_kernel<TX><<<nb, KT, 0, s>>>(w, v, vp, alpha, beta, j, partial, n);
+    finalize(partial, nb, scal, F_LBETA, beta, j + 1, s);
+    lanczos_next_kernel<TX><<<nb, KT, 0, s>>>(vp, v, w, scal, basis ? basis + (int64_t)j * n : nullptr, n);
+  };
+  if (use_graph) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos capture: %s", cudaGetErrorString(e));
+    for (int32_t j = 0; j < steps; ++j) step(j);
+    e = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos graph: %s", cudaGetErrorString(e));
+  } else {
+    for (int32_t j = 0; j < steps; ++j) step(j);
+  }
+  if ((rc = launch_check("lanczos steps"))) return rc;
+  e = cudaMemcpyAsync(alpha_h, alpha, sizeof(double) * (size_t)steps, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(beta_h, beta, sizeof(double) * ((size_t)steps + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos: %s", cudaGetErrorString(e));
+  return PJDS_OK;
+}
+
+extern "C" int pjds_lanczos_workspace_bytes(int32_t n_rows, int32_t n_pad, int32_t vec_dtype, int32_t steps,
+                                            size_t *bytes) {
+  clear_error();
+  if (!bytes || n_rows < 0 || n_pad < n_rows || steps < 0) return set_error(PJDS_EINVAL, "bad arguments");
+  *bytes = lanczos_bytes(n_rows, vec_dtype == PJDS_F64 ? 8 : 4, steps);
+  return PJDS_OK;
+}
+
+extern "C" int pjds_lanczos(const pjds_dev *A, const void *v0, int32_t steps, double *alpha_host, double *beta_host,
+                            void *basis, int32_t use_graph, void *work, size_t work_bytes, void *stream) {
+  clear_error();
+  int rc = check_square_permuted(A, "A");
+  if (rc) return rc;
+  if (steps <= 0 || steps > 100000) return set_error(PJDS_EINVAL, "steps must be in [1, 100000]");
+  if (A->n_rows == 0) return set_error(PJDS_EINVAL, "empty matrix");
+  if (!v0 || !alpha_host || !beta_host || !work) return set_error(PJDS_EINVAL, "a pointer argument is NULL");
+  const int vb = vector_bytes(A->dtype);
+  if (work_bytes < lanczos_bytes(A->n_rows, vb, steps)) return set_error(PJDS_EINVAL, "workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (A->dtype == PJDS_F64)
+    return lanczos_run<double>(A, static_cast<const double *>(v0), steps, alpha_host, beta_host,
+                               static_cast<double *>(basis), use_graph, work, s);
+  return lanczos_run<float>(A, static_cast<const float *>(v0), steps, alpha_host, beta_host,
+                            static_cast<float *>(basis), use_graph, work, s);
+}
+
+// ----------------------------------------------------------------------------- tridiagonal eigenpair (host)
+
+namespace {
+
+// number of eigenvalues of T below t (LDL^T Sturm count)
+int sturm_below(int32_t k, const double *a, const double *b, double t) {
+  int cnt = 0;
+  double d = a[0] - t;
+  const double tiny = DBL_MIN * 1e3;
+  for (int32_t i = 0;; ++i) {
+    if (d == 0.0) d = -tiny;
+    if (d < 0.0) ++cnt;
+    if (i + 1 >= k) break;
+    d = (a[i + 1] - t) - b[i + 1] * b[i + 1] / d;
+  }
+  return cnt;
+}
+
+// Solve (T - t I) z = rhs in place by Gaussian elimination with partial
+// pivoting on the tridiagonal band (rows may swap with the next row).
+void tridiag_solve_pivot(int32_t k, const double *a, const double *b, double t, double *z) {
+  std::vector<double> d(k), du(k, 0.0), du2(k, 0.0), dl(k, 0.0);
+  for (int32_t i = 0; i < k; ++i) d[i] = a[i] - t;
+  for (int32_t i = 0; i + 1 < k; ++i) {
+    du[i] = b[i + 1];
+    dl[i] = b[i + 1];
+  }
+  const double eps = DBL_EPSILON * 4.0;
+  double scale = 0.0;
+  for (int32_t i = 0; i < k; ++i) scale = std::max(scale, fabs(a[i]) + (i ? fabs(b[i]) : 0.0));
+  for (int32_t i = 0; i + 1 < k; ++i) {
+    if (fabs(d[i]) >= fabs(dl[i])) {
+      if (d[i] == 0.0) d[i] = eps * (scale > 0 ? scale : 1.0);
+      const double f = dl[i] / d[i];
+      d[i + 1] -= f * du[i];
+      z[i + 1] -= f * z[i];
+      dl[i] = 0.0;
+    } else {  // swap rows i and i+1
+      const double f = d[i] / dl[i];
+      d[i] = dl[i];
+      const double tmp = d[i + 1];
+      d[i + 1] = du[i] - f * tmp;
+      du[i] = tmp;
+      if (i + 2 < k) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du2[i];
+      }
+      const double zt = z[i];
+      z[i] = z[i + 1];
+      z[i + 1] = zt - f * z[i + 1];
+    }
+  }
+  if (d[k - 1] == 0.0) d[k - 1] = eps * (scale > 0 ? scale : 1.0);
+  z[k - 1] /= d[k - 1];
+  if (k > 1) z[k - 2] = (z[k - 2] - du[k - 2] * z[k - 1]) / d[k - 2];
+  for (int32_t i = k - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / d[i];
+}
+
+}  // namespace
+
+extern "C" int pjds_tridiag_extreme(int32_t k, const double *alpha, const double *beta, int32_t which, double *theta,
+                                    double *s) {
+  clear_error();
+  if (k <= 0 || !alpha || !beta || !theta) return set_error(PJDS_EINVAL, "bad arguments");
+  double lo = alpha[0], hi = alpha[0];
+  for (int32_t i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(beta[i]) : 0.0) + (i + 1 < k ? fabs(beta[i + 1]) : 0.0);
+    lo = std::min(lo, alpha[i] - r);
+    hi = std::max(hi, alpha[i] + r);
+  }
+  const double span = std::max(hi - lo, DBL_MIN);
+  lo -= 1e-12 * span;
+  hi += 1e-12 * span;
+  const int m = which == 0 ? k - 1 : 0;  // index of the wanted eigenvalue (ascending)
+  for (int it = 0; it < 2000; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_below(k, alpha, beta, mid) > m)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  const double th = 0.5 * (lo + hi);
+  *theta = th;
+  if (s) {
+    std::vector<double> z(k, 1.0);
+    for (int it = 0; it < 4; ++it) {
+      tridiag_solve_pivot(k, alpha, beta, th, z.data());
+      double nrm = 0.0;
+      for (double v : z) nrm += v * v;
+      nrm = sqrt(nrm);
+      if (!(nrm > 0.0) || !std::isfinite(nrm)) return set_error(PJDS_EINVAL, "inverse iteration failed");
+      for (double &v : z) v /= nrm;
+    }
+    // sign convention: largest-magnitude component positive
+    int32_t im = 0;
+    for (int32_t i = 1; i < k; ++i)
+      if (fabs(z[i]) > fabs(z[im])) im = i;
+    const double sg = z[im] < 0 ? -1.0 : 1.0;
+    for (int32_t i = 0; i < k; ++i) s[i] = sg * z[i];
+  }
+  return PJDS_OK;
+}
+
+// ----------------------------------------------------------------------------- Ritz refinement
+
+static size_t ritz_bytes(int32_t n, int32_t k) {
+  return align256((size_t)n_blocks_of(n) * 8) + align256(S_COUNT * 8) + align256((size_t)k * 8) +
+         align256((size_t)n * 8);
+}
+
+extern "C" int pjds_ritz_workspace_bytes(int32_t n_rows, int32_t n_pad, int32_t k, size_t *bytes) {
+  clear_error();
+  if (!bytes || n_rows < 0 || n_pad < n_rows || k <= 0) return set_error(PJDS_EINVAL, "bad arguments");
+  *bytes = ritz_bytes(n_rows, k);
+  return PJDS_OK;
+}
+
+extern "C" int pjds_ritz_refine(const pjds_dev *A_hi, const void *basis, int32_t basis_dtype, int32_t k,
+                                const double *s_host, double *y, double *theta, double *rel_residual, void *work,
+                                size_t work_bytes, void *stream) {
+  clear_error();
+  int rc = check_square_permuted(A_hi, "A_hi");
+  if (rc) return rc;
+  if (A_hi->dtype != PJDS_F64) return set_error(PJDS_EINVAL, "A_hi must hold fp64 values");
+  if (k <= 0 || !basis || !s_host || !y || !theta || !rel_residual || !work)
+    return set_error(PJDS_EINVAL, "bad arguments");
+  if (basis_dtype != PJDS_F64 && basis_dtype != PJDS_F32) return set_error(PJDS_EINVAL, "basis must be f64 or f32");
+  const int32_t n = A_hi->n_rows, nb = n_blocks_of(n);
+  if (n == 0) return set_error(PJDS_EINVAL, "empty matrix");
+  if (work_bytes < ritz_bytes(n, k)) return set_error(PJDS_EINVAL, "workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve cv{static_cast<char *>(work), 0, 0};
+  double *partial = cv.take<double>((size_t)nb);
+  double *scal = cv.take<double>(S_COUNT);
+  double *sd = cv.take<double>((size_t)k);
+  double *w = cv.take<double>((size_t)n);
+  cudaError_t e = cudaMemcpyAsync(sd, s_host, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "ritz: %s", cudaGetErrorString(e));
+  if (basis_dtype == PJDS_F64)
+    ritz_combine_kernel<double><<<nb, KT, 0, st>>>(static_cast<const double *>(basis), sd, k, n, y, partial);
+  else
+    ritz_combine_kernel<float><<<nb, KT, 0, st>>>(static_cast<const float *>(basis), sd, k, n, y, partial);
+  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX0, st);              // (y, y)
+  launch_spmv_dot<double, double, 0>(A_hi, y, w, nullptr, partial, st);  // w = A y, (y, w)
+  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX1, st);
+  ritz_residual_kernel<<<nb, KT, 0, st>>>(w, y, scal, partial, n);
+  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX2, st);
+  if ((rc = launch_check("ritz refine"))) return rc;
+  double h[3];
+  e = cudaMemcpyAsync(h, scal + S_AUX0, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "ritz: %s", cudaGetErrorString(e));
+  if (!(h[0] > 0.0)) return set_error(PJDS_EINVAL, "Ritz vector is zero");
+  *theta = h[1] / h[0];
+  *rel_residual = sqrt(h[2] / h[0]) / fabs(*theta);
+  return PJDS_OK;
+}
