@@ -310,6 +310,33 @@ static int launch_check(const char *what) {
   return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Record the launches `body` issues into a graph on a private stream and
+// instantiate it. Nothing executes while capturing.
+template <typename F>
+static int capture_graph(cudaGraphExec_t *exec, F body) {
+  cudaStream_t cap = nullptr;
+  cudaGraph_t g = nullptr;
+  *exec = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "graph stream: %s", cudaGetErrorString(e));
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    body(cap);
+    const cudaError_t e_launch = cudaGetLastError();
+    e = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e_launch;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    if (*exec) cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+    return set_error(PJDS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  return PJDS_OK;
+}
+
 static int check_square_permuted(const pjds_dev *A, const char *name) {
   if (!A) return set_error(PJDS_EINVAL, "%s is NULL", name);
   if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "%s: unknown dtype", name);
@@ -382,24 +409,22 @@ static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, doubl
   if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg: %s", cudaGetErrorString(e));
   const double bnorm = sqrt(bn2);
 
-  auto inner_step = [&]() {
-    spmv_dot_any<TL>(Al, p, q, partial, s);                              // q = A p, (p, q)
-    finalize(partial, nb, scal, F_ALPHA, nullptr, 0, s);                 // alpha
-    cg_update_kernel<TL><<<nb, KT, 0, s>>>(d, r, p, q, scal, partial, n);  // d, r, (r, r)
-    finalize(partial, nb, scal, F_BETA, nullptr, 0, s);                  // beta
-    cg_dir_kernel<TL><<<nb, KT, 0, s>>>(p, r, scal, n);                  // p
+  auto inner_step = [&](cudaStream_t st) {
+    spmv_dot_any<TL>(Al, p, q, partial, st);                               // q = A p, (p, q)
+    finalize(partial, nb, scal, F_ALPHA, nullptr, 0, st);                  // alpha
+    cg_update_kernel<TL><<<nb, KT, 0, st>>>(d, r, p, q, scal, partial, n);  // d, r, (r, r)
+    finalize(partial, nb, scal, F_BETA, nullptr, 0, st);                   // beta
+    cg_dir_kernel<TL><<<nb, KT, 0, st>>>(p, r, scal, n);                   // p
   };
 
   cudaGraphExec_t exec = nullptr;
   if (o.use_graph) {
-    cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg graph capture: %s", cudaGetErrorString(e));
-    for (int it = 0; it < o.inner_iters; ++it) inner_step();
-    e = cudaStreamEndCapture(s, &g);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg graph: %s", cudaGetErrorString(e));
+    // recorded on a private stream (nothing runs during capture; the legacy
+    // default stream cannot be captured), replayed on the caller's stream
+    rc = capture_graph(&exec, [&](cudaStream_t st) {
+      for (int it = 0; it < o.inner_iters; ++it) inner_step(st);
+    });
+    if (rc) return rc;
   }
 
   pjds_cg_result out;
@@ -429,7 +454,7 @@ static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, doubl
         break;
       }
     } else {
-      for (int it = 0; it < o.inner_iters; ++it) inner_step();
+      for (int it = 0; it < o.inner_iters; ++it) inner_step(s);
     }
     ir_correct_kernel<TL><<<nb, KT, 0, s>>>(x, d, scal, n);
     if ((rc = launch_check("cg inner"))) break;
@@ -505,27 +530,24 @@ static int lanczos_run(const pjds_dev *A, const TX *v0, int32_t steps, double *a
   lanczos_start_kernel<TX><<<nb, KT, 0, s>>>(v0, v, vp, scal, n);
   int rc = launch_check("lanczos start");
   if (rc) return rc;
-  auto step = [&](int32_t j) {
-    spmv_dot_any<TX>(A, v, w, partial, s);  // w = A v, (v, w)
-    finalize(partial, nb, scal, F_LALPHA, alpha, j, s);
-    lanczos_orth_kernel<TX><<<nb, KT, 0, s>>>(w, v, vp, alpha, beta, j, partial, n);
-    finalize(partial, nb, scal, F_LBETA, beta, j + 1, s);
-    lanczos_next_kernel<TX><<<nb, KT, 0, s>>>(vp, v, w, scal, basis ? basis + (int64_t)j * n : nullptr, n);
+  auto step = [&](int32_t j, cudaStream_t st) {
+    spmv_dot_any<TX>(A, v, w, partial, st);  // w = A v, (v, w)
+    finalize(partial, nb, scal, F_LALPHA, alpha, j, st);
+    lanczos_orth_kernel<TX><<<nb, KT, 0, st>>>(w, v, vp, alpha, beta, j, partial, n);
+    finalize(partial, nb, scal, F_LBETA, beta, j + 1, st);
+    lanczos_next_kernel<TX><<<nb, KT, 0, st>>>(vp, v, w, scal, basis ? basis + (int64_t)j * n : nullptr, n);
   };
   if (use_graph) {
-    cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
-    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos capture: %s", cudaGetErrorString(e));
-    for (int32_t j = 0; j < steps; ++j) step(j);
-    e = cudaStreamEndCapture(s, &g);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
-    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos graph: %s", cudaGetErrorString(e));
+    rc = capture_graph(&exec, [&](cudaStream_t st) {
+      for (int32_t j = 0; j < steps; ++j) step(j, st);
+    });
+    if (rc) return rc;
+    e = cudaGraphLaunch(exec, s);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos graph launch: %s", cudaGetErrorString(e));
   } else {
-    for (int32_t j = 0; j < steps; ++j) step(j);
+    for (int32_t j = 0; j < steps; ++j) step(j, s);
   }
   if ((rc = launch_check("lanczos steps"))) return rc;
   e = cudaMemcpyAsync(alpha_h, alpha, sizeof(double) * (size_t)steps, cudaMemcpyDeviceToHost, s);
