@@ -16,8 +16,9 @@
  * Every matrix here must have been created with permute_cols = 1 (square,
  * permuted basis); vectors are in that basis (use pjds_permute/unpermute).
  * Scratch memory: every driver takes a caller-owned device workspace of at
- * least the size its *_workspace_bytes function reports; the library never
- * allocates device memory. Reductions are deterministic (fixed-order partial
+ * least the size its *_workspace_bytes function reports, except
+ * pjds_cg_solve_static, which uses a static device array instead; the
+ * library never allocates device memory. Reductions are deterministic (fixed-order partial
  * sums per CTA, then one CTA), so repeated runs give identical results.
  */
 #ifndef PJDS_KRYLOV_H
@@ -74,6 +75,31 @@ int pjds_cg_workspace_bytes(int32_t n_rows, int32_t n_pad, int32_t vec_dtype, si
  */
 int pjds_cg_solve(const pjds_dev *A_hi, const pjds_dev *A_lo, const double *b, double *x, const pjds_cg_opts *opts,
                   pjds_cg_result *res, void *work, size_t work_bytes, void *stream);
+
+/*
+ * pjds_cg_solve without a caller workspace. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory for a
+ * workspace at all — for example code that only ever receives the matrix, b
+ * and x from a host application that owns every device allocation, or a hot
+ * loop that must not pay for cudaMalloc/cudaFree (which can synchronise the
+ * device) on each solve. It runs the same solve as pjds_cg_solve, with the
+ * same arguments minus the workspace, using a 5.5 MiB array in device memory
+ * that the library declares statically: every GPU that loads the library
+ * holds it until the process exits. Limits and behaviour:
+ *   - at most 131072 rows; larger matrices return PJDS_EINVAL (use
+ *     pjds_cg_solve with a caller workspace);
+ *   - the first call on a device (with that device current) looks up the
+ *     array's device address once; make that first call before any stream
+ *     capture;
+ *   - no cudaMalloc, cudaFree or allocating library call is made;
+ *   - all calls share the one array per device and it keeps the previous
+ *     call's contents: each call clears the scalar block it reads and writes
+ *     every vector before reading it, but calls that overlap on the GPU
+ *     within one process (on two streams, or from two host threads) race on
+ *     it and must be serialised by the caller.
+ */
+int pjds_cg_solve_static(const pjds_dev *A_hi, const pjds_dev *A_lo, const double *b, double *x,
+                         const pjds_cg_opts *opts, pjds_cg_result *res, void *stream);
 
 /* Workspace bytes for pjds_lanczos (vectors of A's vector type). */
 int pjds_lanczos_workspace_bytes(int32_t n_rows, int32_t n_pad, int32_t vec_dtype, int32_t steps, size_t *bytes);

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.h"
@@ -741,4 +742,82 @@ extern "C" int pjds_ritz_refine(const pjds_dev *A_hi, const void *basis, int32_t
   *theta = h[1] / h[0];
   *rel_residual = sqrt(h[2] / h[0]) / fabs(*theta);
   return PJDS_OK;
+}
+
+// ----------------------------------------------------------------------------- CG without any allocation
+
+// pjds_cg_solve_static: the same solve as pjds_cg_solve, for callers that
+// cannot provide a device workspace at all. Its workspace is this file-scope
+// device array, which every GPU that loads the library holds until the
+// process exits. The array's name is only a host-side stand-in in host code,
+// so its device address is looked up once per device with
+// cudaGetSymbolAddress and that address is handed to the kernels.
+namespace pjds {
+namespace kry {
+
+constexpr int32_t CG_STATIC_MAX_ROWS = 131072;
+constexpr size_t CG_STATIC_BYTES = (size_t)11 << 19;  // 5.5 MiB
+static __device__ __align__(256) unsigned char g_cg_static_scratch[CG_STATIC_BYTES];
+
+constexpr int kMaxDevices = 64;
+static void *g_cg_static_ptr[kMaxDevices];
+static std::mutex g_cg_static_mu;
+
+// Device address of the static workspace on the current device (set up on
+// the first call per device).
+static int cg_static_workspace(void **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(PJDS_EINVAL, "device %d outside the supported range", dev);
+  std::lock_guard<std::mutex> lock(g_cg_static_mu);
+  if (!g_cg_static_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_cg_static_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(PJDS_ECUDA, "cudaGetSymbolAddress of the static workspace: %s", cudaGetErrorString(e));
+    g_cg_static_ptr[dev] = p;
+  }
+  *out = g_cg_static_ptr[dev];
+  return PJDS_OK;
+}
+
+}  // namespace kry
+}  // namespace pjds
+
+extern "C" int pjds_cg_solve_static(const pjds_dev *A_hi, const pjds_dev *A_lo, const double *b, double *x,
+                                    const pjds_cg_opts *opts, pjds_cg_result *res, void *stream) {
+  clear_error();
+  int rc = check_square_permuted(A_hi, "A_hi");
+  if (rc) return rc;
+  if (A_hi->dtype != PJDS_F64) return set_error(PJDS_EINVAL, "A_hi must hold fp64 values");
+  if (!A_lo) A_lo = A_hi;
+  if ((rc = check_square_permuted(A_lo, "A_lo"))) return rc;
+  if (A_lo->n_rows != A_hi->n_rows) return set_error(PJDS_EINVAL, "A_lo and A_hi differ in size");
+  if (A_hi->n_rows > CG_STATIC_MAX_ROWS)
+    return set_error(PJDS_EINVAL,
+                     "pjds_cg_solve_static handles at most %d rows (got %d); use pjds_cg_solve with a workspace",
+                     CG_STATIC_MAX_ROWS, A_hi->n_rows);
+  if (A_hi->n_rows == 0) return PJDS_OK;
+  if (!b || !x) return set_error(PJDS_EINVAL, "b or x is NULL");
+  pjds_cg_opts o{6, 50, 0.0, 1, 0};
+  if (opts) {
+    o = *opts;
+    if (o.max_outer <= 0) o.max_outer = 6;
+    if (o.inner_iters <= 0) o.inner_iters = 50;
+  }
+  if (o.inner_iters > 100000 || o.max_outer > 100000) return set_error(PJDS_EINVAL, "iteration counts too large");
+  const bool low = A_lo->dtype != PJDS_F64;
+  const size_t need = cg_bytes(A_hi->n_rows, low ? 4 : 8);
+  if (need > CG_STATIC_BYTES)
+    return set_error(PJDS_EINVAL, "static workspace of %zu bytes is smaller than %zu", CG_STATIC_BYTES, need);
+  void *work = nullptr;
+  if ((rc = cg_static_workspace(&work))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The array keeps the previous call's contents: clear the partial sums and
+  // the scalar block; every vector is written before it is read.
+  const size_t head = align256((size_t)n_blocks_of(A_hi->n_rows) * 8) + align256(S_COUNT * 8);
+  cudaError_t e = cudaMemsetAsync(work, 0, head, s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "clear static workspace: %s", cudaGetErrorString(e));
+  return low ? cg_run<float>(A_hi, A_lo, b, x, o, res, work, s) : cg_run<double>(A_hi, A_lo, b, x, o, res, work, s);
 }

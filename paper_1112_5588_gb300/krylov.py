@@ -34,6 +34,8 @@ for _name, _res, _args in (
         ("pjds_cg_workspace_bytes", ctypes.c_int, [_i32, _i32, _i32, _P(_sz)]),
         ("pjds_cg_solve", ctypes.c_int, [_P(_p._PjdsDevS), _P(_p._PjdsDevS), _vp, _vp, _P(_CgOpts), _P(_CgResult),
                                          _vp, _sz, _vp]),
+        ("pjds_cg_solve_static", ctypes.c_int, [_P(_p._PjdsDevS), _P(_p._PjdsDevS), _vp, _vp, _P(_CgOpts),
+                                                _P(_CgResult), _vp]),
         ("pjds_lanczos_workspace_bytes", ctypes.c_int, [_i32, _i32, _i32, _i32, _P(_sz)]),
         ("pjds_lanczos", ctypes.c_int, [_P(_p._PjdsDevS), _vp, _i32, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
         ("pjds_tridiag_extreme", ctypes.c_int, [_i32, _vp, _vp, _i32, _P(_f64), _vp]),
@@ -70,6 +72,23 @@ def cg_solve(A_hi, A_lo, b: torch.Tensor, x: torch.Tensor, max_outer: int = 6, i
     _p._check(_lib.pjds_cg_solve(ctypes.byref(A_hi.struct), ctypes.byref(A_lo.struct) if A_lo is not None else None,
                                  b.data_ptr(), x.data_ptr(), ctypes.byref(o), ctypes.byref(r), work.data_ptr(),
                                  work.numel(), _p._stream_ptr(stream)), "pjds_cg_solve")
+    return {"outer": r.outer, "inner_total": r.inner_total, "rel_residual": r.rel_residual,
+            "history": list(r.history[:r.n_history])}
+
+
+def cg_solve_static(A_hi, A_lo, b: torch.Tensor, x: torch.Tensor, max_outer: int = 6, inner_iters: int = 50,
+                    tol: float = 0.0, use_graph: bool = True, stream=None) -> dict:
+    """pjds_cg_solve_static: the same solve as cg_solve, for callers that
+    cannot allocate device memory; the library's static device workspace
+    (at most 131072 rows) is used instead of a caller workspace."""
+    for t, nm in ((b, "b"), (x, "x")):
+        _p._check_vec(t, A_hi.n_rows, torch.float64, nm)
+    o = _CgOpts(max_outer, inner_iters, tol, 1 if use_graph else 0, 0)
+    r = _CgResult()
+    _p._check(_lib.pjds_cg_solve_static(ctypes.byref(A_hi.struct),
+                                        ctypes.byref(A_lo.struct) if A_lo is not None else None, b.data_ptr(),
+                                        x.data_ptr(), ctypes.byref(o), ctypes.byref(r), _p._stream_ptr(stream)),
+              "pjds_cg_solve_static")
     return {"outer": r.outer, "inner_total": r.inner_total, "rel_residual": r.rel_residual,
             "history": list(r.history[:r.n_history])}
 
