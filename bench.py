@@ -148,6 +148,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1234)
     ap.add_argument("--no-side", action="store_true", help="skip the side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--stencil-g", type=int, default=165, help="grid of the precision (stencil) workload")
+    ap.add_argument("--lanczos-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -270,8 +272,10 @@ def run_ours(args, world, rank, local_rank):
     y_gpu = y.cpu().numpy()
 
     side = {}
+    prec_gpu = None
     if not args.no_side:
         side = side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes)
+        prec_gpu = precision_gpu_leg(torch, pjds, args, dev, flush)
 
     # ---------------- end to end through the C ABI from pinned host memory
     xh = torch.from_numpy(x).pin_memory()
@@ -313,6 +317,8 @@ def run_ours(args, world, rank, local_rank):
                "gflops": round(2 * A.nnz * reps / t_cpu / 1e9, 3)}
         absax = oracle.crs_absmv(A, x)
         err = float(np.max(np.abs(y_gpu - y_ref)) / np.max(absax))
+        if prec_gpu is not None:
+            prec_gpu = precision_oracle_checks(oracle, prec_gpu)
 
     src_hash = kernel_source_hash()
     tr = NCU_TRAFFIC.get(("hmep_f64_pjds", A.n_rows))
@@ -337,6 +343,7 @@ def run_ours(args, world, rank, local_rank):
         "setup_s": {"generate": round(t_gen, 2), "pjds_create": round(t_conv, 2)},
         "kernel_src": src_hash,
         **side,
+        "precision": prec_gpu["report"] if prec_gpu else None,
     }
     print(json.dumps(line), flush=True)
     if dist_on:
@@ -404,6 +411,106 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return {"side": out}
+
+
+def precision_gpu_leg(torch, pjds, args, dev, flush):
+    """Mixed precision on the FEM-like stencil (27-point, 165^3, 10% of pairs
+    dropped, SPD): pJDS products in fp64/fp32/bf16, 300-step CG in fp64 vs
+    fp32/bf16 inner steps with fp64 residual refinement, and 200 Lanczos steps
+    in fp64 vs fp32 with an fp64-refined Ritz pair. Everything runs in the
+    permuted basis. Results are checked against the oracle in the CPU leg."""
+    import synth
+    from paper_1112_5588_gb300 import krylov
+    S = synth.stencil27(g=args.stencil_g, p_drop=0.1, seed=args.seed)
+    n = S.n_rows
+    rep = {"matrix": f"stencil27 g={args.stencil_g} (N={n}, nnz={S.nnz}), SPD, permuted basis"}
+    devs, perm = {}, None
+    for dt in ("f64", "f32", "bf16"):
+        H = pjds.pjds_create(S.n_rows, S.n_cols, S.row_ptr, S.col, S.val, b=32, dtype=dt, permute_cols=True)
+        if perm is None:
+            perm = H.perm.copy()
+        devs[dt] = H.to_device(dev)
+        H.destroy()
+    # kernel-level: the product in each precision
+    xs = torch.from_numpy(synth.vector(n, seed=args.seed)[perm]).to(dev)
+    for dt, D in devs.items():
+        xv = xs.to(D.vec_dtype)
+        yv = torch.empty(n, dtype=D.vec_dtype, device=dev)
+        t = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv(D, xv, yv), 10, 3, flush))
+        vb = {"f64": 8, "f32": 4, "bf16": 2}[dt]
+        xb = 8 if dt == "f64" else 4
+        nb = alg_bytes(n, n, S.nnz, vb, xb, scatter=False)
+        rep[f"spmv_{dt}"] = {"gbs": round(nb / t / 1e9, 1), "us": round(t * 1e6, 2),
+                             "frac_of_hbm": round(nb / t / 1e9 / hbm_peak()[0], 4)}
+    b = synth.vector(n, seed=args.seed + 1)
+    bp = torch.from_numpy(b[perm]).to(dev)
+    runs = {"cg_fp64": (None, 1, 300), "cg_f32_refined": ("f32", 6, 50), "cg_bf16_refined": ("bf16", 12, 25)}
+    xs_out = {}
+    for name, (lo, mo, inner) in runs.items():
+        Dlo = devs[lo] if lo else None
+        work = torch.empty(krylov.cg_workspace_bytes(n, devs["f64"].n_pad, 1 if lo else 0), dtype=torch.uint8,
+                           device=dev)
+        xp = torch.zeros_like(bp)
+        krylov.cg_solve(devs["f64"], Dlo, bp, xp, max_outer=mo, inner_iters=inner, work=work)  # warm-up
+        xp.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = krylov.cg_solve(devs["f64"], Dlo, bp, xp, max_outer=mo, inner_iters=inner, work=work)
+        torch.cuda.synchronize()
+        dt_s = time.perf_counter() - t0
+        x = np.empty(n)
+        x[perm] = xp.cpu().numpy()
+        xs_out[name] = x
+        rep[name] = {"outer": r["outer"], "inner_steps": r["inner_total"], "ms": round(dt_s * 1e3, 2),
+                     "rel_residual_gpu": r["rel_residual"]}
+    # Lanczos: 200 steps fp64 vs fp32 + fp64 Ritz refinement
+    v0 = synth.vector(n, seed=args.seed + 2)[perm]
+    lan, ys = {}, {}
+    for dt in ("f64", "f32"):
+        D = devs[dt]
+        v0t = torch.from_numpy(v0).to(dev, D.vec_dtype)
+        krylov.lanczos(D, v0t, 20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        alpha, beta, V = krylov.lanczos(D, v0t, args.lanczos_steps, keep_basis=True)
+        torch.cuda.synchronize()
+        t_l = time.perf_counter() - t0
+        th, svec = krylov.tridiag_extreme(alpha, beta)
+        yv, th_ref, resid = krylov.ritz_refine(devs["f64"], V, svec)
+        y_o = np.empty(n)
+        y_o[perm] = yv.cpu().numpy()
+        lan[dt] = {"ms_recurrence": round(t_l * 1e3, 2), "theta_T": th, "theta_refined_fp64": th_ref,
+                   "rel_residual_gpu": resid}
+        ys[dt] = y_o
+        del V
+        torch.cuda.empty_cache()
+    rep["lanczos_steps"] = args.lanczos_steps
+    rep["lanczos"] = lan
+    if "f64" in lan and "f32" in lan:
+        rep["theta_refined_f32_vs_f64_rel"] = abs(lan["f32"]["theta_refined_fp64"] -
+                                                  lan["f64"]["theta_refined_fp64"]) / abs(lan["f64"]["theta_refined_fp64"])
+    f64 = rep["cg_fp64"]["ms"]
+    for name in ("cg_f32_refined", "cg_bf16_refined"):
+        rep[name]["speedup_vs_fp64"] = round(f64 / rep[name]["ms"], 3)
+    del devs
+    torch.cuda.empty_cache()
+    return {"S": S, "b": b, "x": xs_out, "ys": ys, "report": rep}
+
+
+def precision_oracle_checks(oracle, pg):
+    """CPU leg: fp64 oracle residuals of the GPU solutions and Ritz pairs."""
+    S, b, rep = pg["S"], pg["b"], pg["report"]
+    bn = float(np.linalg.norm(b))
+    for name, x in pg["x"].items():
+        rep[name]["rel_residual_oracle"] = float(np.linalg.norm(b - oracle.crs_spmv(S, x)) / bn)
+    for dt, y in pg["ys"].items():
+        L = rep["lanczos"][dt]
+        Ay = oracle.crs_spmv(S, y)
+        rq = float(y @ Ay / (y @ y))
+        L["theta_oracle_rayleigh"] = rq
+        L["rel_residual_oracle"] = float(np.linalg.norm(Ay - rq * y) / np.linalg.norm(y) / abs(rq))
+    pg["report"] = rep
+    return pg
 
 
 if __name__ == "__main__":
