@@ -8,7 +8,8 @@ and the two share no code. The arithmetic lives in ``oracle.c``, compiled with
 Every function states the passage of Kreutzer et al., "Sparse matrix-vector
 multiplication on GPGPU clusters" (arXiv:1112.5588) it follows; see oracle.c.
 Pins for each function (dense brute force, closed forms, invariants, hand-worked
-fixtures) are in tests/test_oracle_pins.py.
+fixtures) are in tests/test_oracle_pins.py; the Krylov oracles (krylov.py) are
+pinned in tests/test_oracle_krylov.py.
 """
 from __future__ import annotations
 
@@ -50,6 +51,8 @@ def _load():
         lib.oracle_crs_spmv.restype = None
         lib.oracle_crs_absmv.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.oracle_crs_absmv.restype = None
+        lib.oracle_crs_spmm.argtypes = [i64, vp, vp, vp, i64, vp, vp]
+        lib.oracle_crs_spmm.restype = None
         lib.oracle_crs_spmv_rows.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp]
         lib.oracle_crs_spmv_rows.restype = None
         lib.oracle_pjds_shape.argtypes = [i64, vp, i64, vp]
@@ -102,6 +105,16 @@ def crs_absmv(A, x: np.ndarray) -> np.ndarray:
     s = np.empty(A.n_rows, np.float64)
     _load().oracle_crs_absmv(A.n_rows, _p(rp), _p(col), _p(val), _p(x), _p(s))
     return s
+
+
+def crs_spmm(A, X: np.ndarray) -> np.ndarray:
+    """Y = A X, X of shape (n_cols, k), fp64, CRS order for every column."""
+    X = _c(X, np.float64)
+    k = X.shape[1]
+    rp, col, val = _c(A.row_ptr, np.int64), _c(A.col, np.int32), _c(A.val, np.float64)
+    Y = np.empty((A.n_rows, k), np.float64)
+    _load().oracle_crs_spmm(A.n_rows, _p(rp), _p(col), _p(val), k, _p(X), _p(Y))
+    return Y
 
 
 def crs_spmv_rows(A, x: np.ndarray, rows: np.ndarray):

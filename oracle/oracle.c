@@ -85,6 +85,20 @@ void oracle_crs_absmv(int64_t n_rows, const int64_t *row_ptr, const int32_t *col
   }
 }
 
+/* Y = A X for k right-hand sides, X (n_cols x k) and Y (n_rows x k) row-major:
+ * Y[i][c] = sum_k val_k * X[col_k][c], CRS order per (i, c) — the definition of
+ * k independent products y_c = A x_c (block product of the batched solvers). */
+void oracle_crs_spmm(int64_t n_rows, const int64_t *row_ptr, const int32_t *col, const double *val, int64_t k,
+                     const double *X, double *Y) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n_rows; ++i)
+    for (int64_t c = 0; c < k; ++c) {
+      double s = 0.0;
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s = s + val[e] * X[(int64_t)col[e] * k + c];
+      Y[i * k + c] = s;
+    }
+}
+
 /* Evaluate only the listed rows (for sampled checks at full size). */
 void oracle_crs_spmv_rows(const int64_t *row_ptr, const int32_t *col, const double *val, const double *x,
                           const int64_t *rows, int64_t n_sel, double *y_sel, double *abs_sel) {

@@ -98,6 +98,23 @@ def test_crs_spmv_threads_do_not_change_result(oracle_lib):
     assert np.array_equal(y1, y2)
 
 
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_crs_spmm_equals_dense_and_columnwise(oracle_lib, k):
+    A = tiny.random_lengths(70, 40, max_len=40, seed=k, integer_values=True)
+    X = np.random.default_rng(k).integers(-3, 4, (40, k)).astype(np.float64)
+    Y = oracle_lib.crs_spmm(A, X)
+    assert np.array_equal(Y, pins.dense_of(A) @ X)
+    B = tiny.random_lengths(50, 60, max_len=30, seed=k + 10)
+    Xf = np.random.default_rng(k + 1).uniform(-1, 1, (60, k))
+    Yf = oracle_lib.crs_spmm(B, Xf)
+    for c in range(k):  # same per-(row, column) order as the single product
+        assert np.array_equal(Yf[:, c], oracle_lib.crs_spmv(B, Xf[:, c].copy()))
+    # a transposed right-hand-side layout (column-major X) must be caught
+    if k > 1:
+        Xt = np.ascontiguousarray(Xf.T).reshape(Xf.shape)
+        assert not np.array_equal(oracle_lib.crs_spmm(B, Xt), Yf)
+
+
 # ----------------------------------------------------------------------------- Oracle B
 
 def _golden(golden_dir):
