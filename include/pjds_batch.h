@@ -1,0 +1,77 @@
+/*
+ * pjds_batch.h — batched pJDS products on one GPU:
+ *   - pjds_spmm: one matrix, k right-hand sides (block product Y = A X);
+ *   - pjds_batch_*: many matrices of uneven sizes in one persistent launch.
+ *
+ * Paper (arXiv:1112.5588): the product is the dominant step of iterative
+ * solvers (Sect. 1.1) and is bandwidth bound (Eq. 1); reading the matrix once
+ * for k vectors divides its bytes per flop by k, and one persistent launch
+ * over many small matrices removes per-launch overhead and tail imbalance.
+ * Conventions as in pjds.h (statuses, caller-owned device memory, streams).
+ */
+#ifndef PJDS_BATCH_H
+#define PJDS_BATCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pjds.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Y = A X for k right-hand sides. X: n_cols x k, Y: n_rows x k, row-major
+ * (element (r, c) at r*k + c), device memory of A's vector type (double for
+ * PJDS_F64, float otherwise), 16-byte aligned. k: 1, or a multiple of 4 up to
+ * 128 (float) / a multiple of 2 up to 64 (double). Each thread handles one
+ * row and 16 bytes of its k columns, so the lanes of a row read each
+ * gathered row of X as one contiguous segment. Column c of Y is computed in
+ * the same order and with the same fused multiply-adds as pjds_spmv with one
+ * thread per row on column c of X. Original basis (permute_cols = 0): row i of
+ * the sorted matrix is written to row perm[i] of Y; permuted basis: to row i.
+ */
+int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream);
+
+/* Opaque host handle of a batch plan. */
+typedef struct pjds_batch pjds_batch;
+
+/*
+ * Device bytes of the plan for these matrices: a work counter, one
+ * descriptor per matrix and one entry per tile of 256 sorted rows.
+ */
+int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes);
+
+/*
+ * Build a plan for y_m = A_m x_m, m < n_mats. mats[m] are device views of
+ * pJDS matrices of one dtype (original or permuted basis each); xs[m], ys[m]
+ * their device vectors. The tiles of all matrices are ordered by their
+ * stored work, largest first, and copied into plan_dev (caller-owned device
+ * memory of pjds_batch_plan_bytes). Reads each matrix's block lengths back
+ * to the host once. *out receives a host handle (free with
+ * pjds_batch_destroy). Errors: PJDS_EINVAL (mixed dtypes, sizes), ENOMEM,
+ * ECUDA.
+ */
+int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                      void *plan_dev, size_t plan_bytes, pjds_batch **out, void *stream);
+
+/*
+ * Run the plan: reset the work counter and launch one persistent kernel
+ * (one CTA per SM slot) whose CTAs take tiles from the counter until none is
+ * left. use_graph = 1 records the two steps once into a CUDA graph kept in
+ * the handle and replays it (the handle's first run with use_graph must not
+ * happen while the stream is capturing).
+ */
+int pjds_batch_run(pjds_batch *h, int32_t use_graph, void *stream);
+
+/* Number of tiles and CTAs of the plan (for reporting). */
+int pjds_batch_info(const pjds_batch *h, int32_t *n_tiles, int32_t *n_ctas);
+
+int pjds_batch_destroy(pjds_batch *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PJDS_BATCH_H */

@@ -19,6 +19,8 @@
  *   oracle_crs_spmv        y = A x in CRS order (Sect. 1.1 problem statement;
  *                          the CRS CPU baseline of Table 1).
  *   oracle_crs_absmv       |A| |x|, the scale of the forward error bound.
+ *   oracle_crs_spmm        Y = A X for k right-hand sides (k independent
+ *                          products, each in CRS order).
  *   oracle_pjds_shape/fill pJDS conversion, Sect. 2.1: sort rows by descending
  *                          length, pad each block of b consecutive rows to the
  *                          block's longest row, store the padded matrix column

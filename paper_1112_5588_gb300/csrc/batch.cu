@@ -1,0 +1,396 @@
+// Batched pJDS products (include/pjds_batch.h): the block product Y = A X for
+// k right-hand sides, and one persistent launch over many matrices.
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "common.h"
+#include "pjds_batch.h"
+#include "spmv_kernels.cuh"
+
+namespace pjds {
+namespace bat {
+
+constexpr int BT = 256;  // threads per CTA; one batch tile = BT sorted rows
+
+// 16-byte vectors of the vector type
+template <typename TX>
+struct V16;
+template <>
+struct V16<float> {
+  static constexpr int W = 4;
+  __device__ static void load(const float *p, float (&v)[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  }
+  __device__ static void store(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct V16<double> {
+  static constexpr int W = 2;
+  __device__ static void load(const double *p, double (&v)[2]) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    v[0] = a.x, v[1] = a.y;
+  }
+  __device__ static void store(double *p, const double (&v)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// Thread t: sorted row i = t / lr, columns [q W, q W + W) of its k, q = t % lr.
+template <typename TV, typename TX, typename IDX, bool SCATTER>
+__global__ void __launch_bounds__(BT)
+    spmm_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ col_start,
+                const int32_t *__restrict__ block_len, const int32_t *__restrict__ perm, const TX *__restrict__ X,
+                TX *__restrict__ Y, int32_t n_rows, int32_t b, int32_t k, int32_t lr) {
+  using TA = typename dev::Acc<TV>::T;
+  constexpr int W = V16<TX>::W, U = 4;
+  const int64_t t = (int64_t)blockIdx.x * BT + threadIdx.x;
+  const int64_t i = t / lr;
+  const int32_t q = (int32_t)(t % lr);
+  if (i >= n_rows) return;
+  const int32_t L = __ldg(block_len + (int32_t)(i / b));
+  TA acc[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc[w] = TA(0);
+  for (int32_t j = 0; j < L; j += U) {
+    int32_t c[U];
+    TV v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < L) {
+        const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i;
+        c[u] = __ldcs(col + o);
+        v[u] = dev::ld_stream1(val + o);
+      } else {
+        c[u] = -1;
+        v[u] = TV{};
+      }
+    }
+    TX xv[U][W];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (c[u] >= 0) {
+        V16<TX>::load(X + (int64_t)c[u] * k + (int64_t)q * W, xv[u]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) xv[u][w] = TX(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        acc[w] = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u][w], acc[w]) : acc[w];
+  }
+  TX out[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) out[w] = (TX)acc[w];
+  const int64_t r = SCATTER ? (int64_t)__ldcs(perm + i) : i;
+  V16<TX>::store(Y + r * k + (int64_t)q * W, out);
+}
+
+// ----------------------------------------------------------------------------- persistent batch
+
+struct Desc {
+  const void *val;
+  const int32_t *col;
+  const int64_t *col_start;
+  const int32_t *block_len;
+  const int32_t *perm;
+  const void *x;
+  void *y;
+  int32_t n_rows, b, scatter, idx64;
+};
+
+template <typename TV, typename TX, typename IDX>
+__device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int64_t i) {
+  using TA = typename dev::Acc<TV>::T;
+  constexpr int U = 4;
+  const TV *__restrict__ val = static_cast<const TV *>(d.val);
+  const TX *__restrict__ x = static_cast<const TX *>(d.x);
+  const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
+  TA acc = TA(0);
+  for (int32_t j = 0; j < L; j += U) {
+    int32_t c[U];
+    TV v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < L) {
+        const IDX o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
+        c[u] = __ldcs(d.col + o);
+        v[u] = dev::ld_stream1(val + o);
+      } else {
+        c[u] = -1;
+        v[u] = TV{};
+      }
+    }
+    TX xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = dev::gather(x, c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
+  }
+  return acc;
+}
+
+// CTAs take tiles (matrix, first sorted row) from a work counter until none
+// is left; a tile's rows are one per thread. No CTA ever waits for another.
+template <typename TV, typename TX>
+__global__ void __launch_bounds__(BT)
+    batch_kernel(const Desc *__restrict__ descs, const int2 *__restrict__ tiles, int32_t n_tiles,
+                 int32_t *__restrict__ counter) {
+  __shared__ int32_t s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int32_t t = s_tile;
+    __syncthreads();
+    if (t >= n_tiles) return;
+    const int2 tl = tiles[t];
+    const Desc d = descs[tl.x];
+    const int64_t i = (int64_t)tl.y + threadIdx.x;
+    if (i < d.n_rows) {
+      const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
+      TX *y = static_cast<TX *>(d.y);
+      y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
+    }
+  }
+}
+
+static inline size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace bat
+}  // namespace pjds
+
+using namespace pjds;
+using namespace pjds::bat;
+
+struct pjds_batch {
+  int32_t dtype, n_mats, n_tiles, n_ctas;
+  int32_t *counter;
+  const Desc *descs;
+  const int2 *tiles;
+  cudaGraphExec_t exec;
+};
+
+// ----------------------------------------------------------------------------- spmm
+
+template <typename TV, typename TX>
+static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cudaStream_t s) {
+  constexpr int W = V16<TX>::W;
+  const int32_t lr = k / W;
+  const int64_t threads = (int64_t)A->n_rows * lr;
+  const int64_t grid = (threads + BT - 1) / BT;
+  if (grid <= 0) return PJDS_OK;
+  if (grid > 0x7fffffffLL) return set_error(PJDS_EOVERFLOW, "grid too large");
+  const TV *val = static_cast<const TV *>(A->val);
+  const TX *x = static_cast<const TX *>(X);
+  TX *y = static_cast<TX *>(Y);
+  const bool small = A->n_stored + A->n_pad < 0x7fffffffLL, sc = !A->permute_cols;
+#define SPMM(IDX, SC)                                                                                       \
+  spmm_kernel<TV, TX, IDX, SC><<<(unsigned)grid, BT, 0, s>>>(val, A->col, A->col_start, A->block_len, A->perm, x, \
+                                                              y, A->n_rows, A->b, k, lr)
+  if (small) {
+    if (sc) SPMM(int32_t, true);
+    else SPMM(int32_t, false);
+  } else {
+    if (sc) SPMM(int64_t, true);
+    else SPMM(int64_t, false);
+  }
+#undef SPMM
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "pjds_spmm launch: %s", cudaGetErrorString(e));
+}
+
+extern "C" int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream) {
+  clear_error();
+  if (!A) return set_error(PJDS_EINVAL, "A is NULL");
+  if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "unknown dtype %d", A->dtype);
+  if (k == 1) return pjds_spmv(A, X, Y, stream);
+  const int w = A->dtype == PJDS_F64 ? 2 : 4;
+  if (k < w || k % w || k > 32 * w)
+    return set_error(PJDS_EINVAL, "k = %d: use 1 or a multiple of %d up to %d", k, w, 32 * w);
+  if (A->n_rows < 0 || A->n_cols < 1 || A->b <= 0 || A->b % 32 ||
+      (int64_t)A->n_pad != ((int64_t)A->n_rows + A->b - 1) / A->b * A->b)
+    return set_error(PJDS_EINVAL, "inconsistent matrix sizes");
+  if (A->n_rows == 0) return PJDS_OK;
+  if (!X || !Y) return set_error(PJDS_EINVAL, "X or Y is NULL");
+  if (((uintptr_t)X | (uintptr_t)Y) & 15) return set_error(PJDS_EINVAL, "X and Y must be 16-byte aligned");
+  if (A->n_stored > 0 && (!A->val || !A->col || !A->col_start || !A->block_len))
+    return set_error(PJDS_EINVAL, "a matrix array is NULL");
+  if (!A->permute_cols && !A->perm) return set_error(PJDS_EINVAL, "perm is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (A->n_stored == 0) {
+    cudaError_t e = cudaMemsetAsync(Y, 0, (size_t)A->n_rows * k * vector_bytes(A->dtype), s);
+    return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  switch (A->dtype) {
+    case PJDS_F64: return launch_spmm<double, double>(A, k, X, Y, s);
+    case PJDS_F32: return launch_spmm<float, float>(A, k, X, Y, s);
+    default: return launch_spmm<dev::bf16_t, float>(A, k, X, Y, s);
+  }
+}
+
+// ----------------------------------------------------------------------------- batch
+
+static int64_t tiles_of(const pjds_dev &A) { return ((int64_t)A.n_rows + BT - 1) / BT; }
+
+extern "C" int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes) {
+  clear_error();
+  if (n_mats <= 0 || !mats || !bytes) return set_error(PJDS_EINVAL, "bad arguments");
+  int64_t nt = 0;
+  for (int32_t m = 0; m < n_mats; ++m) nt += tiles_of(mats[m]);
+  *bytes = a256(sizeof(int32_t)) + a256(sizeof(Desc) * (size_t)n_mats) + a256(sizeof(int2) * (size_t)nt);
+  return PJDS_OK;
+}
+
+extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                                 void *plan_dev, size_t plan_bytes, pjds_batch **out, void *stream) {
+  clear_error();
+  if (n_mats <= 0 || !mats || !xs || !ys || !plan_dev || !out) return set_error(PJDS_EINVAL, "bad arguments");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = pjds_batch_plan_bytes(n_mats, mats, &need);
+  if (rc) return rc;
+  if (plan_bytes < need) return set_error(PJDS_EINVAL, "plan buffer of %zu bytes is smaller than %zu", plan_bytes, need);
+  const int32_t dt = mats[0].dtype;
+  if (value_bytes(dt) == 0) return set_error(PJDS_EINVAL, "unknown dtype");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<Desc> descs((size_t)n_mats);
+  struct T {
+    int32_t m, row0;
+    int64_t cost;
+  };
+  std::vector<T> tiles;
+  for (int32_t m = 0; m < n_mats; ++m) {
+    const pjds_dev &A = mats[m];
+    if (A.dtype != dt) return set_error(PJDS_EINVAL, "matrix %d has another dtype than matrix 0", m);
+    if (A.n_rows < 0 || A.b <= 0 || A.b % 32 || (int64_t)A.n_pad != ((int64_t)A.n_rows + A.b - 1) / A.b * A.b)
+      return set_error(PJDS_EINVAL, "matrix %d: inconsistent sizes", m);
+    if (A.n_rows > 0 && (!xs[m] || !ys[m])) return set_error(PJDS_EINVAL, "matrix %d: x or y is NULL", m);
+    if (A.n_stored > 0 && (!A.val || !A.col || !A.col_start || !A.block_len))
+      return set_error(PJDS_EINVAL, "matrix %d: a matrix array is NULL", m);
+    if (A.n_rows > 0 && !A.permute_cols && !A.perm) return set_error(PJDS_EINVAL, "matrix %d: perm is NULL", m);
+    Desc &d = descs[(size_t)m];
+    d.val = A.val;
+    d.col = A.col;
+    d.col_start = A.col_start;
+    d.block_len = A.block_len;
+    d.perm = A.perm;
+    d.x = xs[m];
+    d.y = ys[m];
+    d.n_rows = A.n_rows;
+    d.b = A.b;
+    d.scatter = A.permute_cols ? 0 : 1;
+    d.idx64 = A.n_stored + A.n_pad < 0x7fffffffLL ? 0 : 1;
+    if (A.n_rows == 0) continue;
+    // block lengths back to the host once, to weigh the tiles
+    std::vector<int32_t> bl((size_t)A.n_blocks);
+    cudaError_t e = cudaMemcpyAsync(bl.data(), A.block_len, sizeof(int32_t) * bl.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "read block lengths: %s", cudaGetErrorString(e));
+    for (int64_t t0 = 0; t0 < A.n_rows; t0 += BT) {
+      int64_t cost = 0;
+      for (int64_t r = t0; r < std::min<int64_t>(t0 + BT, A.n_pad); r += A.b) cost += (int64_t)bl[(size_t)(r / A.b)];
+      tiles.push_back(T{m, (int32_t)t0, cost});
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const T &a, const T &b) { return a.cost > b.cost; });
+  std::vector<int2> tl(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i) tl[i] = make_int2(tiles[i].m, tiles[i].row0);
+  char *p = static_cast<char *>(plan_dev);
+  int32_t *counter = reinterpret_cast<int32_t *>(p);
+  Desc *dd = reinterpret_cast<Desc *>(p + a256(sizeof(int32_t)));
+  int2 *td = reinterpret_cast<int2 *>(p + a256(sizeof(int32_t)) + a256(sizeof(Desc) * (size_t)n_mats));
+  cudaError_t e = cudaMemcpyAsync(dd, descs.data(), sizeof(Desc) * descs.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !tl.empty())
+    e = cudaMemcpyAsync(td, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "upload plan: %s", cudaGetErrorString(e));
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (dt == PJDS_F64)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double, double>, BT, 0);
+  else if (dt == PJDS_F32)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float, float>, BT, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<dev::bf16_t, float>, BT, 0);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "occupancy: %s", cudaGetErrorString(e));
+  pjds_batch *h = static_cast<pjds_batch *>(calloc(1, sizeof(pjds_batch)));
+  if (!h) return set_error(PJDS_ENOMEM, "out of host memory");
+  h->dtype = dt;
+  h->n_mats = n_mats;
+  h->n_tiles = (int32_t)tl.size();
+  h->n_ctas = std::max(1, std::min(sms * std::max(per_sm, 1), std::max(h->n_tiles, 1)));
+  h->counter = counter;
+  h->descs = dd;
+  h->tiles = td;
+  h->exec = nullptr;
+  *out = h;
+  return PJDS_OK;
+}
+
+static int batch_issue(pjds_batch *h, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(h->counter, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "reset counter: %s", cudaGetErrorString(e));
+  if (h->dtype == PJDS_F64)
+    batch_kernel<double, double><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
+  else if (h->dtype == PJDS_F32)
+    batch_kernel<float, float><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
+  else
+    batch_kernel<dev::bf16_t, float><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+}
+
+extern "C" int pjds_batch_run(pjds_batch *h, int32_t use_graph, void *stream) {
+  clear_error();
+  if (!h) return set_error(PJDS_EINVAL, "h is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->n_tiles == 0) return PJDS_OK;
+  if (!use_graph) return batch_issue(h, s);
+  if (!h->exec) {
+    cudaStream_t cap = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "graph stream: %s", cudaGetErrorString(e));
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int rc = PJDS_OK;
+    if (e == cudaSuccess) {
+      rc = batch_issue(h, cap);
+      e = cudaStreamEndCapture(cap, &g);
+    }
+    if (rc == PJDS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (rc != PJDS_OK) return rc;
+    if (e != cudaSuccess) {
+      h->exec = nullptr;
+      return set_error(PJDS_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(h->exec, s);
+  return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "batch graph launch: %s", cudaGetErrorString(e));
+}
+
+extern "C" int pjds_batch_info(const pjds_batch *h, int32_t *n_tiles, int32_t *n_ctas) {
+  clear_error();
+  if (!h) return set_error(PJDS_EINVAL, "h is NULL");
+  if (n_tiles) *n_tiles = h->n_tiles;
+  if (n_ctas) *n_ctas = h->n_ctas;
+  return PJDS_OK;
+}
+
+extern "C" int pjds_batch_destroy(pjds_batch *h) {
+  clear_error();
+  if (!h) return PJDS_OK;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  free(h);
+  return PJDS_OK;
+}

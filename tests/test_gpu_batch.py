@@ -1,0 +1,139 @@
+"""GPU batched products: pjds_spmm against the oracle's block product and,
+column by column, bit for bit against pjds_spmv with one thread per row; the
+persistent multi-matrix launch against the oracle and the single products."""
+import numpy as np
+import pytest
+
+import synth
+from synth import tiny
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1112_5588_gb300 import build
+    build.build()
+    from paper_1112_5588_gb300 import batch, pjds
+    return torch, pjds, batch
+
+
+SHAPES = [("dlr", lambda: synth.block_dense(n_brow=3000, bs=4, nb=36, frac=0.05, seed=3)),
+          ("zipf", lambda: synth.zipf_rows(20_000, s=2.0, len_max=512, seed=4)),
+          ("ragged", lambda: tiny.random_lengths(1037, 900, max_len=70, seed=5, p_empty=0.2))]
+
+
+@pytest.mark.parametrize("dtype,k", [("f64", 2), ("f64", 8), ("f64", 32), ("f32", 4), ("f32", 16), ("f32", 32),
+                                     ("f32", 128), ("bf16", 8)])
+@pytest.mark.parametrize("name,make", SHAPES, ids=[s[0] for s in SHAPES])
+def test_spmm_matches_oracle_and_columnwise_spmv(mods, oracle_lib, dtype, k, name, make):
+    torch, pjds, batch = mods
+    A = make()
+    X = np.random.default_rng(k).uniform(-1, 1, (A.n_cols, k))
+    if dtype != "f64":
+        X = X.astype(np.float32).astype(np.float64)
+    H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype)
+    D = H.to_device("cuda")
+    Xt = torch.from_numpy(X).to("cuda", D.vec_dtype).contiguous()
+    Yt = torch.full((A.n_rows, k), float("nan"), dtype=D.vec_dtype, device="cuda")
+    batch.spmm(D, Xt, Yt)
+    torch.cuda.synchronize()
+    Y = Yt.double().cpu().numpy()
+    Ar = A if dtype == "f64" else A._replace(
+        val=oracle_lib.round_f32(A.val) if dtype == "f32" else oracle_lib.round_bf16(A.val))
+    Yr = oracle_lib.crs_spmm(Ar, X)
+    S = oracle_lib.crs_spmm(Ar._replace(val=np.abs(Ar.val)), np.abs(X))
+    lens = np.diff(A.row_ptr)
+    check = parity.check_fp64 if dtype == "f64" else parity.check_fp32
+    for c in range(k):
+        r = check(Y[:, c], Yr[:, c], S[:, c], lens)
+        assert r["ok"], (c, r)
+    # same arithmetic as the single product, column by column
+    for c in (0, k - 1):
+        y1 = torch.empty(A.n_rows, dtype=D.vec_dtype, device="cuda")
+        pjds.pjds_spmv_cfg(D, Xt[:, c].contiguous(), y1, threads_per_row=1, rows_per_thread=1)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, Yt[:, c].contiguous())
+
+
+def test_spmm_permuted_basis_and_k1(mods):
+    torch, pjds, batch = mods
+    A = synth.stencil27(g=16, seed=2)
+    H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f32", permute_cols=True)
+    D = H.to_device("cuda")
+    X = torch.rand(A.n_rows, 8, device="cuda")
+    Y = torch.empty_like(X)
+    batch.spmm(D, X, Y)
+    for c in range(8):
+        y1 = torch.empty(A.n_rows, device="cuda")
+        pjds.pjds_spmv_cfg(D, X[:, c].contiguous(), y1, threads_per_row=1)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, Y[:, c].contiguous())
+    X1 = X[:, :1].contiguous()
+    Y1 = torch.empty(A.n_rows, 1, device="cuda")
+    batch.spmm(D, X1, Y1)
+    y1 = torch.empty(A.n_rows, device="cuda")
+    pjds.pjds_spmv(D, X1.reshape(-1), y1)
+    torch.cuda.synchronize()
+    assert torch.equal(Y1.reshape(-1), y1)
+
+
+def test_spmm_rejects_bad_k(mods):
+    torch, pjds, batch = mods
+    A = tiny.random_lengths(64, 64, max_len=8, seed=1)
+    D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype="f32").to_device("cuda")
+    for k in (3, 6, 132):
+        with pytest.raises(pjds.PjdsError):
+            batch.spmm(D, torch.zeros(64, k, device="cuda"), torch.zeros(64, k, device="cuda"))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_uneven_matrices(mods, oracle_lib, dtype, graph):
+    torch, pjds, batch = mods
+    rng = np.random.default_rng(7)
+    sizes = np.exp(rng.uniform(np.log(300), np.log(60_000), 24)).astype(int)
+    mats, devs, xs, ys, xh = [], [], [], [], []
+    for m, n in enumerate(sizes):
+        A = synth.zipf_rows(int(n), s=2.0, len_max=512, seed=100 + m) if m % 3 else \
+            tiny.random_lengths(int(n), int(n), max_len=min(40, int(n)), seed=m, p_empty=0.1)
+        H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype,
+                             permute_cols=(m % 4 == 1))
+        D = H.to_device("cuda")
+        x = synth.vector(A.n_cols, seed=m)
+        if dtype == "f32":
+            x = x.astype(np.float32).astype(np.float64)
+        xin = x[H.perm] if m % 4 == 1 else x
+        mats.append((A, H.perm.copy(), m % 4 == 1))
+        devs.append(D)
+        xs.append(torch.from_numpy(xin).to("cuda", D.vec_dtype))
+        ys.append(torch.full((A.n_rows,), float("nan"), dtype=D.vec_dtype, device="cuda"))
+        xh.append(x)
+    B = batch.Batch(devs, xs, ys)
+    info = B.info()
+    assert info["n_tiles"] == sum((A.n_rows + 255) // 256 for A, _, _ in mats)
+    for _ in range(2):
+        for y in ys:
+            y.fill_(float("nan"))
+        B.run(use_graph=graph)
+        torch.cuda.synchronize()
+        for (A, perm, permuted), x, y, D in zip(mats, xh, ys, devs):
+            got = y.double().cpu().numpy()
+            if permuted:
+                g2 = np.empty_like(got)
+                g2[perm] = got
+                got = g2
+            Ar = A if dtype == "f64" else A._replace(val=oracle_lib.round_f32(A.val))
+            check = parity.check_fp64 if dtype == "f64" else parity.check_fp32
+            r = check(got, oracle_lib.crs_spmv(Ar, x), oracle_lib.crs_absmv(Ar, x), np.diff(A.row_ptr))
+            assert r["ok"], r
+    # bit for bit the single product with one thread per row
+    A, perm, permuted = mats[2]
+    y1 = torch.empty_like(ys[2])
+    pjds.pjds_spmv_cfg(devs[2], xs[2], y1, threads_per_row=1)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, ys[2])
+    B.destroy()
