@@ -276,6 +276,7 @@ def run_ours(args, world, rank, local_rank):
     if not args.no_side:
         side = side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes)
         prec_gpu = precision_gpu_leg(torch, pjds, args, dev, flush)
+        side["side"]["batching"] = batching_leg(torch, pjds, args, dev, flush)
 
     # ---------------- end to end through the C ABI from pinned host memory
     xh = torch.from_numpy(x).pin_memory()
@@ -495,6 +496,72 @@ def precision_gpu_leg(torch, pjds, args, dev, flush):
     del devs
     torch.cuda.empty_cache()
     return {"S": S, "b": b, "x": xs_out, "ys": ys, "report": rep}
+
+
+def batching_leg(torch, pjds, args, dev, flush):
+    """Block product with k right-hand sides on the DLR-like matrix (dense
+    4x4 blocks, 36 block columns within +-5%: N = 280k, 144 nonzeros/row,
+    fp32 values and vectors), and 64 uneven matrices (N log-uniform in
+    [10k, 500k], Zipf(2) row lengths capped at 512, fp64) in one persistent
+    launch replayed as a CUDA graph vs one launch per matrix."""
+    import synth
+    from paper_1112_5588_gb300 import batch
+    out = {}
+    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=args.seed)
+    H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f32")
+    D = H.to_device(dev)
+    H.destroy()
+    spmm = {"matrix": f"DLR-like N={A.n_rows} nnz={A.nnz}", "dtype": "f32"}
+    for k in (1, 4, 8, 16, 32):
+        X = torch.rand(A.n_cols, k, device=dev)
+        Y = torch.empty(A.n_rows, k, device=dev)
+        t = statistics.median(time_launches(torch, lambda: batch.spmm(D, X, Y), 10, 3, flush))
+        nb = A.nnz * 8 + 4 * k * (A.n_cols + A.n_rows) + 4 * A.n_rows
+        spmm[f"k{k}"] = {"us": round(t * 1e6, 2), "gbs": round(nb / t / 1e9, 1),
+                         "gflops": round(2 * A.nnz * k / t / 1e9, 1),
+                         "us_per_rhs": round(t * 1e6 / k, 2)}
+    out["spmm"] = spmm
+    del D
+    rng = np.random.default_rng(args.seed)
+    sizes = np.exp(rng.uniform(np.log(10_000), np.log(500_000), 64)).astype(int)
+    devs, xs, ys, nnz, nbytes = [], [], [], 0, 0
+    for m, n in enumerate(sizes):
+        M = synth.zipf_rows(int(n), s=2.0, len_max=512, seed=args.seed + m)
+        Hm = pjds.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32, dtype="f64")
+        devs.append(Hm.to_device(dev))
+        Hm.destroy()
+        xs.append(torch.from_numpy(synth.vector(M.n_cols, seed=m)).to(dev))
+        ys.append(torch.empty(M.n_rows, dtype=torch.float64, device=dev))
+        nnz += M.nnz
+        nbytes += alg_bytes(M.n_rows, M.n_cols, M.nnz, 8, 8)
+    B = batch.Batch(devs, xs, ys)
+    t_batch = statistics.median(time_launches(torch, lambda: B.run(use_graph=True), 10, 3, flush))
+
+    def separate():
+        for Dm, xm, ym in zip(devs, xs, ys):
+            pjds.pjds_spmv(Dm, xm, ym)
+    t_sep = statistics.median(time_launches(torch, separate, 10, 3, flush))
+    # the same 64 launches recorded once into a CUDA graph (no host overhead)
+    g = torch.cuda.CUDAGraph()
+    side_stream = torch.cuda.Stream()
+    side_stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side_stream):
+        separate()
+    torch.cuda.current_stream().wait_stream(side_stream)
+    with torch.cuda.graph(g):
+        separate()
+    t_sep_graph = statistics.median(time_launches(torch, g.replay, 10, 3, flush))
+    out["multi_matrix"] = {"n_mats": 64, "total_rows": int(sizes.sum()), "nnz": int(nnz), **B.info(),
+                           "persistent_graph_us": round(t_batch * 1e6, 2),
+                           "persistent_graph_gbs": round(nbytes / t_batch / 1e9, 1),
+                           "separate_launches_us": round(t_sep * 1e6, 2),
+                           "separate_launches_graph_us": round(t_sep_graph * 1e6, 2),
+                           "speedup_vs_separate": round(t_sep / t_batch, 3),
+                           "speedup_vs_separate_graph": round(t_sep_graph / t_batch, 3)}
+    B.destroy()
+    del devs, xs, ys
+    torch.cuda.empty_cache()
+    return out
 
 
 def precision_oracle_checks(oracle, pg):
