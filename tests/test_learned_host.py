@@ -1,0 +1,60 @@
+"""Learned tuner host logic: features, candidate encoding, model init and scaling."""
+import numpy as np
+import pytest
+
+import synth
+from synth import tiny
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1112_5588_gb300 import build
+    build.build()
+    from paper_1112_5588_gb300 import learned
+    return learned
+
+
+def test_features_against_numpy(L):
+    for A in (synth.zipf_rows(5000, s=1.7, len_max=300, seed=2), tiny.random_lengths(300, 900, max_len=50, seed=1),
+              synth.hmep_like(n=20_000, seed=3)):
+        f = L.features(A)
+        lens = np.diff(A.row_ptr).astype(np.float64)
+        rows = np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr))
+        d = np.abs(A.col.astype(np.float64) - rows)
+        mu, sd = lens.mean(), lens.std()
+        want = [np.log10(A.n_rows), np.log10(A.nnz), np.log2(1 + mu), sd / mu, ((lens - mu) ** 3).mean() / sd ** 3,
+                np.log2(1 + lens.max()), d.mean() / A.n_rows, np.mean(d <= 64)]
+        assert np.allclose(f, want, rtol=1e-5, atol=1e-6), (f, want)
+
+
+def test_encode(L):
+    f = np.arange(8, dtype=np.float32)
+    cands = [{"b": 32, "dtype": "f64", "threads_per_row": 1}, {"b": 256, "dtype": "bf16", "threads_per_row": 8},
+             {"b": 64, "dtype": "f32", "threads_per_row": 0}]
+    X = L.encode(f, cands)
+    assert X.shape == (3, 13)
+    assert np.array_equal(X[:, :8], np.tile(f, (3, 1)))
+    assert np.array_equal(X[:, 8:], [[0, 0, 1, 0, 0], [3, 3, 0, 0, 1], [1, 0, 0, 1, 0]])
+
+
+def test_init_and_scaling(L):
+    m = L.init(5)
+    w1 = np.array(m.w1)
+    assert np.all(np.abs(w1) <= np.sqrt(6 / 13)) and w1.std() > 0.3
+    assert np.array_equal(np.array(L.init(5).w2), np.array(m.w2))
+    X = np.random.default_rng(0).standard_normal((100, 13)).astype(np.float32) * 3 + 1
+    X[:, 4] = 2.0  # constant column keeps std 1
+    y = np.random.default_rng(1).standard_normal(100).astype(np.float32)
+    L.fit_scaling(m, X, y)
+    assert np.allclose(m.in_mean, X.mean(0), atol=1e-5)
+    assert np.allclose(np.array(m.in_std)[[0, 1, 2, 3, 5]], X.std(0)[[0, 1, 2, 3, 5]], rtol=1e-5)
+    assert m.in_std[4] == 1.0
+    assert m.out_mean == pytest.approx(y.mean(), abs=1e-6) and m.out_std == pytest.approx(y.std(), rel=1e-5)
+
+
+def test_model_json_roundtrip(L, tmp_path):
+    m = L.init(9)
+    p = tmp_path / "m.json"
+    L.save(m, str(p), {"note": "test"})
+    m2 = L.load(str(p))
+    assert np.array_equal(np.array(m.w2), np.array(m2.w2)) and m.b3 == m2.b3
