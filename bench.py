@@ -405,7 +405,7 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
     del Dp, xp, yp
 
     for cfg in ({"rows_per_thread": 2}, {"rows_per_thread": 4}, {"threads_per_row": 2}, {"block_threads": 512},
-                {"block_threads": 128}):
+                {"block_threads": 128}, {"staged": 1}):
         tc = med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xt, y, **cfg), K, W, flush))
         key = "cfg_" + "_".join(f"{k}{v}" for k, v in cfg.items())
         out[key] = {"gbs": round(nbytes / tc / 1e9, 1), "us": round(tc * 1e6, 2)}
@@ -437,12 +437,13 @@ def precision_gpu_leg(torch, pjds, args, dev, flush):
     for dt, D in devs.items():
         xv = xs.to(D.vec_dtype)
         yv = torch.empty(n, dtype=D.vec_dtype, device=dev)
-        t = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv(D, xv, yv), 10, 3, flush))
         vb = {"f64": 8, "f32": 4, "bf16": 2}[dt]
         xb = 8 if dt == "f64" else 4
         nb = alg_bytes(n, n, S.nnz, vb, xb, scatter=False)
-        rep[f"spmv_{dt}"] = {"gbs": round(nb / t / 1e9, 1), "us": round(t * 1e6, 2),
-                             "frac_of_hbm": round(nb / t / 1e9 / hbm_peak()[0], 4)}
+        for tag, kw in (("", {}), ("_staged", {"staged": 1})):
+            t = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xv, yv, **kw), 10, 3, flush))
+            rep[f"spmv_{dt}{tag}"] = {"gbs": round(nb / t / 1e9, 1), "us": round(t * 1e6, 2),
+                                      "frac_of_hbm": round(nb / t / 1e9 / hbm_peak()[0], 4)}
     b = synth.vector(n, seed=args.seed + 1)
     bp = torch.from_numpy(b[perm]).to(dev)
     runs = {"cg_fp64": (None, 1, 300), "cg_f32_refined": ("f32", 6, 50), "cg_bf16_refined": ("bf16", 12, 25)}

@@ -145,7 +145,17 @@ int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
  *                    (0 = default);
  *   unroll           jagged diagonals loaded per round of the j-loop
  *                    (0 = default; R=1: 4, 8, 16; R=2: 2, 4, 8; R=4: 2, 4;
- *                    T>1: 2, 4).
+ *                    T>1: 2, 4);
+ *   staged           1: a persistent kernel (one CTA per SM slot, tiles of
+ *                    128 sorted rows) whose producer warp copies each tile's
+ *                    jagged-diagonal runs of val and col into a 3-stage
+ *                    shared-memory ring with bulk copies (cp.async.bulk,
+ *                    mbarrier completion) while 4 consumer warps gather x
+ *                    and accumulate; one thread per row, block_threads and
+ *                    unroll are ignored, val and col must be 16-byte aligned.
+ *                    Its waits are bounded; a wait that runs out sets a bit
+ *                    in the device status word (pjds_device_status) and the
+ *                    affected rows of y are not written.
  * rows_per_thread > 1 and threads_per_row > 1 are exclusive. Invalid values
  * return PJDS_EINVAL.
  */
@@ -154,6 +164,8 @@ typedef struct pjds_launch {
   int32_t threads_per_row;
   int32_t block_threads;
   int32_t unroll;
+  int32_t staged;
+  int32_t reserved[3];
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
@@ -166,6 +178,14 @@ int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *
  * vice versa. Returns PJDS_EINVAL for a combination pjds_spmv_cfg rejects.
  */
 int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *out);
+
+/*
+ * Device status word of the staged kernel (see pjds_launch.staged): 0 when
+ * every wait completed since the last clear, else bit 0 (a consumer wait ran
+ * out) / bit 1 (a producer wait ran out). clear = 1 resets it. Waits for the
+ * stream.
+ */
+int pjds_device_status(int32_t *status, int32_t clear, void *stream);
 
 /*
  * End-to-end product from host memory: copies x_host (n_cols elements) into

@@ -31,6 +31,8 @@ typedef struct pjds_candidate {
   int32_t threads_per_row; /* as in pjds_launch (0 = default) */
   int32_t block_threads;   /* as in pjds_launch (0 = default) */
   int32_t unroll;          /* as in pjds_launch (0 = default) */
+  int32_t staged;          /* as in pjds_launch */
+  int32_t reserved;
 } pjds_candidate;
 
 typedef struct pjds_tune_entry {

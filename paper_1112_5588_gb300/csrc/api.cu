@@ -41,6 +41,11 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   if (R != 1 && R != 2 && R != 4) return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
   if (T != 1 && T != 2 && T != 4 && T != 8) return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
   if (R > 1 && T > 1) return set_error(PJDS_EINVAL, "rows_per_thread > 1 needs threads_per_row = 1");
+  if (c.staged) {
+    if (R != 1 || T != 1) return set_error(PJDS_EINVAL, "the staged kernel runs one thread per row");
+    if (((uintptr_t)A->val | (uintptr_t)A->col) & 15)
+      return set_error(PJDS_EINVAL, "the staged kernel needs 16-byte aligned val and col");
+  }
   if (c.unroll == 0) c.unroll = T > 1 ? 4 : (R == 1 ? (A->dtype == PJDS_F32 ? 8 : 4) : (R == 2 ? 4 : 2));
   const int U = c.unroll;
   const bool u_ok = T > 1 ? (U == 2 || U == 4)
@@ -68,6 +73,7 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   c.threads_per_row = A->n_max >= 64 ? 2 : 1;
   c.block_threads = A->dtype == PJDS_F32 ? 256 : 128;
   c.unroll = 0;  // filled in by check_cfg once R and T are final
+  c.staged = 0;
   return c;
 }
 
@@ -96,6 +102,11 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->threads_per_row > 1 && !cfg->rows_per_thread) c.rows_per_thread = 1;
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
     if (cfg->unroll) c.unroll = cfg->unroll;
+    if (cfg->staged) {
+      c.staged = 1;
+      if (!cfg->rows_per_thread) c.rows_per_thread = 1;
+      if (!cfg->threads_per_row) c.threads_per_row = 1;
+    }
   }
   return check_cfg(A, c);
 }
@@ -112,6 +123,8 @@ extern "C" int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds
   out->threads_per_row = c.threads_per_row;
   out->block_threads = c.block_threads;
   out->unroll = c.unroll;
+  out->staged = c.staged;
+  out->reserved[0] = out->reserved[1] = out->reserved[2] = 0;
   return PJDS_OK;
 }
 
@@ -123,6 +136,19 @@ extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pj
   rc = resolve_cfg(A, cfg, c);
   if (rc) return rc;
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pjds_device_status(int32_t *status, int32_t clear, void *stream) {
+  clear_error();
+  if (!status) return set_error(PJDS_EINVAL, "status is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int a = 0, b = 0, c = 0;
+  int e = staged_status_f64(&a, clear != 0, s);
+  if (e == 0) e = staged_status_f32(&b, clear != 0, s);
+  if (e == 0) e = staged_status_bf16(&c, clear != 0, s);
+  if (e != 0) return set_error(PJDS_ECUDA, "reading the device status: %s", cudaGetErrorString((cudaError_t)e));
+  *status = a | b | c;
+  return PJDS_OK;
 }
 
 extern "C" int pjds_spmv_host(const pjds_dev *A, const void *x_host, void *y_host, void *x_dev, void *y_dev,

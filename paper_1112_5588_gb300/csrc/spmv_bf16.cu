@@ -11,4 +11,8 @@ int ellr_launch_bf16(const ellr_dev *A, const void *x, void *y, int nt, cudaStre
   return launch_ellr<dev::bf16_t, float>(A, x, y, nt, s);
 }
 
+int staged_status_bf16(int *out, bool clear, cudaStream_t s) {
+  return (int)dev::staged_status(out, clear, s);
+}
+
 }  // namespace pjds

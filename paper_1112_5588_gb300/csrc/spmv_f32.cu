@@ -11,4 +11,8 @@ int ellr_launch_f32(const ellr_dev *A, const void *x, void *y, int nt, cudaStrea
   return launch_ellr<float, float>(A, x, y, nt, s);
 }
 
+int staged_status_f32(int *out, bool clear, cudaStream_t s) {
+  return (int)dev::staged_status(out, clear, s);
+}
+
 }  // namespace pjds

@@ -11,4 +11,8 @@ int ellr_launch_f64(const ellr_dev *A, const void *x, void *y, int nt, cudaStrea
   return launch_ellr<double, double>(A, x, y, nt, s);
 }
 
+int staged_status_f64(int *out, bool clear, cudaStream_t s) {
+  return (int)dev::staged_status(out, clear, s);
+}
+
 }  // namespace pjds

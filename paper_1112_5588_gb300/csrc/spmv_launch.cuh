@@ -6,6 +6,7 @@
 
 #include "common.h"
 #include "spmv_kernels.cuh"
+#include "spmv_staged.cuh"
 
 namespace pjds {
 
@@ -14,6 +15,7 @@ struct LaunchCfg {
   int threads_per_row;  // T: 1, 2, 4, 8
   int block_threads;    // CTA size
   int unroll;           // U: jagged diagonals per chunk of the j-loop
+  int staged;           // 1: bulk-copy staged persistent kernel (R = T = 1)
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -24,7 +26,26 @@ inline int check_launch(const char *what) {
 }
 
 template <typename TV, typename TX, typename IDX, bool SC>
+int launch_staged(const pjds_dev *A, const TX *x, TX *y, cudaStream_t s) {
+  const TV *val = static_cast<const TV *>(A->val);
+  const int n_tiles = (A->n_pad + dev::ST_TR - 1) / dev::ST_TR;
+  if (n_tiles <= 0) return PJDS_OK;
+  int device = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&device);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::pjds_staged_kernel<TV, TX, IDX, SC>,
+                                                                dev::ST_TR + 32, 0);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "occupancy: %s", cudaGetErrorString(e));
+  int grid = sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > n_tiles) grid = n_tiles;
+  dev::pjds_staged_kernel<TV, TX, IDX, SC><<<grid, dev::ST_TR + 32, 0, s>>>(
+      val, A->col, A->col_start, A->block_len, A->perm, x, y, A->n_rows, A->n_pad, A->b);
+  return check_launch("pjds_spmv staged launch");
+}
+
+template <typename TV, typename TX, typename IDX, bool SC>
 int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaStream_t s) {
+  if (c.staged) return launch_staged<TV, TX, IDX, SC>(A, x, y, s);
   const TV *val = static_cast<const TV *>(A->val);
   const int R = c.rows_per_thread, T = c.threads_per_row, nt = c.block_threads;
   const int64_t work = T > 1 ? (int64_t)A->n_pad * T : ((int64_t)A->n_pad + R - 1) / R;
@@ -115,5 +136,8 @@ int pjds_launch_bf16(const pjds_dev *A, const void *x, void *y, const LaunchCfg 
 int ellr_launch_f64(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
 int ellr_launch_f32(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
 int ellr_launch_bf16(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
+int staged_status_f64(int *out, bool clear, cudaStream_t s);
+int staged_status_f32(int *out, bool clear, cudaStream_t s);
+int staged_status_bf16(int *out, bool clear, cudaStream_t s);
 
 }  // namespace pjds

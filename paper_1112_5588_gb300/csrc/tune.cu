@@ -179,6 +179,8 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
       if (done[i] || cands[i].b != b || cands[i].dtype != dt) continue;
       done[i] = 1;
       pjds_launch in, res;
+      memset(&in, 0, sizeof(in));
+      in.staged = cands[i].staged;
       in.rows_per_thread = cands[i].rows_per_thread;
       in.threads_per_row = cands[i].threads_per_row;
       in.block_threads = cands[i].block_threads;
@@ -193,6 +195,7 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
       out[i].cand.threads_per_row = res.threads_per_row;
       out[i].cand.block_threads = res.block_threads;
       out[i].cand.unroll = res.unroll;
+      out[i].cand.staged = res.staged;
       std::vector<float> t((size_t)reps);
       int lr = PJDS_OK;
       for (int w = 0; w < 2 && lr == PJDS_OK; ++w) lr = pjds_spmv_cfg(&d, x, y, &res, stream);

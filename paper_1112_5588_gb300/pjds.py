@@ -52,7 +52,8 @@ class _PjdsDevS(ctypes.Structure):
 
 
 class _LaunchS(ctypes.Structure):
-    _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32)]
+    _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32),
+                ("staged", _i32), ("reserved", _i32 * 3)]
 
 
 class _EllrHostS(ctypes.Structure):
@@ -82,6 +83,7 @@ def _load_lib():
         "pjds_spmv_cfg": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, P(_LaunchS), _vp]),
         "pjds_spmv_host": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp, _vp, _vp]),
         "pjds_spmv_resolve": (ctypes.c_int, [P(_PjdsDevS), P(_LaunchS), P(_LaunchS)]),
+        "pjds_device_status": (ctypes.c_int, [P(_i32), _i32, _vp]),
         "pjds_permute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_unpermute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "ellr_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, P(P(_EllrHostS))]),
@@ -254,26 +256,34 @@ def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> t
 
 
 def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
-                  threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, stream=None) -> torch.Tensor:
+                  threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, staged: int = 0,
+                  stream=None) -> torch.Tensor:
     """y = A x with an explicit kernel configuration (pjds_spmv_cfg)."""
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y
 
 
 def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, block_threads: int = 0,
-                      unroll: int = 0) -> dict:
+                      unroll: int = 0, staged: int = 0) -> dict:
     """The launch configuration pjds_spmv_cfg would use (no launch). `A` is a
     PjdsDevice or a PjdsHost (only sizes and alignment are read)."""
     s = A.struct if isinstance(A, PjdsDevice) else _dev_struct_from_host(A)
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged)
     out = _LaunchS()
     _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
-            "block_threads": out.block_threads, "unroll": out.unroll}
+            "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged}
+
+
+def pjds_device_status(clear: bool = True, stream=None) -> int:
+    """The staged kernel's device status word (0 = every wait completed)."""
+    st = _i32()
+    _check(_lib.pjds_device_status(ctypes.byref(st), 1 if clear else 0, _stream_ptr(stream)), "pjds_device_status")
+    return st.value
 
 
 def _dev_struct_from_host(H: "PjdsHost"):

@@ -17,7 +17,7 @@ DTYPE_NAMES = {0: "f64", 1: "f32", 2: "bf16"}
 
 class _Cand(ctypes.Structure):
     _fields_ = [("b", _i32), ("dtype", _i32), ("rows_per_thread", _i32), ("threads_per_row", _i32),
-                ("block_threads", _i32), ("unroll", _i32)]
+                ("block_threads", _i32), ("unroll", _i32), ("staged", _i32), ("reserved", _i32)]
 
 
 class _Entry(ctypes.Structure):
@@ -35,7 +35,8 @@ for _name, _args in (("pjds_tune_arena_bytes", [_i32, _i32, _vp, _P(_Cand), _i32
 
 def _cand_dict(c) -> dict:
     return {"b": c.b, "dtype": DTYPE_NAMES.get(c.dtype, c.dtype), "rows_per_thread": c.rows_per_thread,
-            "threads_per_row": c.threads_per_row, "block_threads": c.block_threads, "unroll": c.unroll}
+            "threads_per_row": c.threads_per_row, "block_threads": c.block_threads, "unroll": c.unroll,
+            "staged": c.staged}
 
 
 def default_space(dtypes=("f64",)) -> list:
@@ -53,7 +54,8 @@ def _to_cands(cands) -> ctypes.Array:
     arr = (_Cand * len(cands))()
     for i, c in enumerate(cands):
         arr[i] = _Cand(int(c["b"]), _p._dtype_code(c.get("dtype", "f64")), int(c.get("rows_per_thread", 0)),
-                       int(c.get("threads_per_row", 0)), int(c.get("block_threads", 0)), int(c.get("unroll", 0)))
+                       int(c.get("threads_per_row", 0)), int(c.get("block_threads", 0)), int(c.get("unroll", 0)),
+                       int(c.get("staged", 0)), 0)
     return arr
 
 

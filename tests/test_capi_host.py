@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(P):
 
 
 def test_abi_version_and_struct_sizes(P):
-    assert P.lib().pjds_version() == 1  # the binding itself checked the struct sizes on load
+    assert P.lib().pjds_version() == 2  # the binding itself checked the struct sizes on load
 
 
 CASES = [
@@ -191,10 +191,25 @@ def test_gpu_test_configs_resolve_on_host(P):
 def test_resolve_defaults(P):
     A = synth.hmep_like(n=10_000, seed=1)
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
-    assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128, "unroll": 4}
+    assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128, "unroll": 4,
+                                      "staged": 0}
     Z = synth.zipf_rows(10_000, s=2.0, len_max=512, seed=1)
     HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
     assert P.pjds_spmv_resolve(HZ)["threads_per_row"] == 2
     assert P.pjds_spmv_resolve(HZ, rows_per_thread=2)["threads_per_row"] == 1
     with pytest.raises(P.PjdsError):
         P.pjds_spmv_resolve(HZ, unroll=16)
+
+
+def test_staged_option_resolves(P):
+    A = synth.hmep_like(n=10_000, seed=1)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    r = P.pjds_spmv_resolve(H, staged=1)
+    assert r["staged"] == 1 and r["rows_per_thread"] == 1 and r["threads_per_row"] == 1
+    with pytest.raises(P.PjdsError):
+        P.pjds_spmv_resolve(H, staged=1, rows_per_thread=2)
+    s = P._dev_struct_from_host(H)
+    s.val = 520  # 8-byte aligned only
+    cfg = P._LaunchS(0, 0, 0, 0, 1)
+    out = P._LaunchS()
+    assert P.lib().pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)) == -1

@@ -33,7 +33,7 @@ def stencil():
     return synth.stencil27(g=165, p_drop=0.1, seed=1234)
 
 
-def _spmv(P, A, x, dtype="f64", fmt="pjds"):
+def _spmv(P, A, x, dtype="f64", fmt="pjds", cfg=None):
     import torch
     if fmt == "pjds":
         H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype)
@@ -43,7 +43,10 @@ def _spmv(P, A, x, dtype="f64", fmt="pjds"):
     H.destroy()
     xt = torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=D.vec_dtype)
     y = torch.full((A.n_rows,), float("nan"), dtype=D.vec_dtype, device="cuda")
-    (P.pjds_spmv if fmt == "pjds" else P.ellr_spmv)(D, xt, y)
+    if cfg:
+        P.pjds_spmv_cfg(D, xt, y, **cfg)
+    else:
+        (P.pjds_spmv if fmt == "pjds" else P.ellr_spmv)(D, xt, y)
     torch.cuda.synchronize()
     out = y.cpu().numpy().astype(np.float64)
     del D, xt, y
@@ -57,6 +60,15 @@ def test_hmep_fp64_full(P, oracle_lib, hmep, fmt):
     y = _spmv(P, hmep, x, fmt=fmt)
     r = parity.check_fp64(y, oracle_lib.crs_spmv(hmep, x), oracle_lib.crs_absmv(hmep, x), np.diff(hmep.row_ptr))
     assert r["ok"], r
+
+
+def test_hmep_fp64_staged_full(P, oracle_lib, hmep):
+    x = synth.vector(hmep.n_cols, seed=1)
+    P.pjds_device_status(clear=True)
+    y = _spmv(P, hmep, x, cfg=dict(staged=1))
+    r = parity.check_fp64(y, oracle_lib.crs_spmv(hmep, x), oracle_lib.crs_absmv(hmep, x), np.diff(hmep.row_ptr))
+    assert r["ok"], r
+    assert P.pjds_device_status() == 0
 
 
 def test_hmep_fp32_full(P, oracle_lib, hmep):

@@ -75,6 +75,7 @@ CONFIGS = [
     dict(threads_per_row=2), dict(threads_per_row=4), dict(threads_per_row=8, block_threads=512),
     dict(threads_per_row=1, unroll=4), dict(threads_per_row=1, unroll=16), dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=2, unroll=2),
     dict(rows_per_thread=4, unroll=4), dict(threads_per_row=4, unroll=2), dict(threads_per_row=2, block_threads=32),
+    dict(staged=1),
 ]
 CONFIG_SHAPES = [SHAPES[1], SHAPES[4], SHAPES[6]]
 
@@ -107,7 +108,7 @@ def test_rows_per_thread_bit_identical_to_one_row(P):
     x = synth.vector(A.n_cols, seed=9)
     y1, _, _ = run_pjds(P, A, x, cfg=dict(rows_per_thread=1, threads_per_row=1))
     for cfg in (dict(rows_per_thread=2), dict(rows_per_thread=4), dict(threads_per_row=1, unroll=8),
-                dict(threads_per_row=1, unroll=16),
+                dict(threads_per_row=1, unroll=16), dict(staged=1),
                 dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=4, unroll=4)):
         yR, _, _ = run_pjds(P, A, x, cfg=cfg)
         assert np.array_equal(y1.view(np.uint64), yR.view(np.uint64)), cfg
@@ -124,6 +125,31 @@ def test_ellr_fp64_matches_oracle_and_pjds_bitwise(P, oracle_lib, name, make):
     # same per-row order and fused multiply-add in both kernels (one thread per row)
     yp, _, _ = run_pjds(P, A, x, cfg=dict(threads_per_row=1))
     assert np.array_equal(ye.view(np.uint64), yp.view(np.uint64))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("b", [32, 256])
+def test_staged_kernel_bitwise_and_status(P, dtype, b):
+    # the bulk-copy staged kernel does each row's arithmetic exactly like the
+    # one-thread-per-row kernel; its bounded waits must all complete
+    torch = _torch()
+    for A in (synth.hmep_like(n=300_000, seed=31), synth.zipf_rows(70_000, s=1.8, len_max=512, seed=32),
+              tiny.random_lengths(1037, 800, max_len=70, seed=3, p_empty=0.15)):
+        x = synth.vector(A.n_cols, seed=5)
+        P.pjds_device_status(clear=True)
+        y1, _, _ = run_pjds(P, A, x, b=b, dtype=dtype, cfg=dict(threads_per_row=1, rows_per_thread=1))
+        ys, _, _ = run_pjds(P, A, x, b=b, dtype=dtype, cfg=dict(staged=1))
+        assert np.array_equal(y1, ys)
+        Hp = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b, dtype=dtype,
+                           permute_cols=A.n_rows == A.n_cols)
+        Dp = Hp.to_device("cuda")
+        xt = torch.from_numpy(x).to("cuda", Dp.vec_dtype)
+        ya, yb = (torch.empty(A.n_rows, dtype=Dp.vec_dtype, device="cuda") for _ in range(2))
+        P.pjds_spmv_cfg(Dp, xt, ya, threads_per_row=1)
+        P.pjds_spmv_cfg(Dp, xt, yb, staged=1)
+        torch.cuda.synchronize()
+        assert torch.equal(ya, yb)
+        assert P.pjds_device_status() == 0
 
 
 def test_row_sums_exact(P, oracle_lib):
