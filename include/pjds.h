@@ -188,6 +188,15 @@ int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *ou
 int pjds_device_status(int32_t *status, int32_t clear, void *stream);
 
 /*
+ * Failure-detection self-test of the staged kernel's bounded waits: launches
+ * one thread that waits on an mbarrier nothing completes (which = 0: as a
+ * consumer, which = 1: as the producer). The wait gives up after its limit
+ * (well under a second), sets status bit `which` and the kernel returns; the
+ * context stays usable. Read the bit with pjds_device_status.
+ */
+int pjds_wait_selftest(int32_t which, void *stream);
+
+/*
  * End-to-end product from host memory: copies x_host (n_cols elements) into
  * the caller's device buffer x_dev, runs pjds_spmv into y_dev, copies y_dev
  * back into y_host (n_rows elements) and waits for the stream. Host buffers

@@ -151,6 +151,12 @@ extern "C" int pjds_device_status(int32_t *status, int32_t clear, void *stream) 
   return PJDS_OK;
 }
 
+extern "C" int pjds_wait_selftest(int32_t which, void *stream) {
+  clear_error();
+  if (which != 0 && which != 1) return set_error(PJDS_EINVAL, "which must be 0 or 1");
+  return staged_wait_selftest(which, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int pjds_spmv_host(const pjds_dev *A, const void *x_host, void *y_host, void *x_dev, void *y_dev,
                               void *stream) {
   clear_error();

@@ -11,6 +11,11 @@ int ellr_launch_f64(const ellr_dev *A, const void *x, void *y, int nt, cudaStrea
   return launch_ellr<double, double>(A, x, y, nt, s);
 }
 
+int staged_wait_selftest(int which, cudaStream_t s) {
+  dev::staged_wait_selftest_kernel<<<1, 32, 0, s>>>(which);
+  return check_launch("wait self-test launch");
+}
+
 int staged_status_f64(int *out, bool clear, cudaStream_t s) {
   return (int)dev::staged_status(out, clear, s);
 }

@@ -137,6 +137,7 @@ int ellr_launch_f64(const ellr_dev *A, const void *x, void *y, int nt, cudaStrea
 int ellr_launch_f32(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
 int ellr_launch_bf16(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s);
 int staged_status_f64(int *out, bool clear, cudaStream_t s);
+int staged_wait_selftest(int which, cudaStream_t s);
 int staged_status_f32(int *out, bool clear, cudaStream_t s);
 int staged_status_bf16(int *out, bool clear, cudaStream_t s);
 

@@ -179,6 +179,18 @@ __global__ void __launch_bounds__(ST_TR + 32)
   }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// will complete (which = 0: a fresh barrier's phase 0, as a consumer would;
+// which = 1: the same wait from a producer's side) and must give up and set
+// the matching status bit. No copy is ever issued, so nothing is in flight.
+static __global__ void staged_wait_selftest_kernel(int which) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(&bar, 0)) atomicOr(&g_staged_status, which == 0 ? 1 : 2);
+}
+
 // Read (and optionally clear) this translation unit's status word; waits for the stream.
 inline cudaError_t staged_status(int *out, bool clear, cudaStream_t s) {
   cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_staged_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s);

@@ -84,6 +84,7 @@ def _load_lib():
         "pjds_spmv_host": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp, _vp, _vp]),
         "pjds_spmv_resolve": (ctypes.c_int, [P(_PjdsDevS), P(_LaunchS), P(_LaunchS)]),
         "pjds_device_status": (ctypes.c_int, [P(_i32), _i32, _vp]),
+        "pjds_wait_selftest": (ctypes.c_int, [_i32, _vp]),
         "pjds_permute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_unpermute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "ellr_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, P(P(_EllrHostS))]),
@@ -277,6 +278,11 @@ def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, blo
     _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
             "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged}
+
+
+def pjds_wait_selftest(which: int = 0, stream=None) -> None:
+    """Launch the bounded-wait self-test (pjds_wait_selftest)."""
+    _check(_lib.pjds_wait_selftest(which, _stream_ptr(stream)), "pjds_wait_selftest")
 
 
 def pjds_device_status(clear: bool = True, stream=None) -> int:

@@ -1,0 +1,88 @@
+"""Run one pJDS product case a few times, for profiling under ncu.
+
+    python -m paper_1112_5588_gb300.profile_cases --matrix stencil --g 100 --dtype f64 --permuted --staged --reps 3
+
+Builds one seeded synthetic matrix, converts it, uploads it and launches the
+chosen product `--reps` times (after `--warmup` launches) on the current
+stream, then prints one JSON line with the CUDA-event time of each launch.
+Matrices: hmep (--n rows), stencil (--g grid), dlr (--n rows, 144/row), zipf
+(--n rows). Kinds: spmv (default), ellr, spmm (--k right-hand sides).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+import numpy as np
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--matrix", choices=["hmep", "stencil", "dlr", "zipf"], default="hmep")
+    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--g", type=int, default=100)
+    ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
+    ap.add_argument("--kind", choices=["spmv", "ellr", "spmm"], default="spmv")
+    ap.add_argument("--k", type=int, default=8)
+    ap.add_argument("--permuted", action="store_true")
+    ap.add_argument("--staged", action="store_true")
+    ap.add_argument("--threads-per-row", type=int, default=0)
+    ap.add_argument("--rows-per-thread", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=1234)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    import synth
+    from . import batch, pjds
+
+    if a.matrix == "hmep":
+        A = synth.hmep_like(n=a.n, seed=a.seed)
+    elif a.matrix == "stencil":
+        A = synth.stencil27(g=a.g, seed=a.seed)
+    elif a.matrix == "dlr":
+        A = synth.block_dense(n_brow=max(1, a.n // 4), bs=4, nb=36, frac=0.05, seed=a.seed)
+    else:
+        A = synth.zipf_rows(a.n, s=2.0, len_max=512, seed=a.seed)
+    dev = torch.device("cuda")
+    if a.kind == "ellr":
+        D = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype=a.dtype).to_device(dev)
+    else:
+        D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=a.dtype,
+                             permute_cols=a.permuted).to_device(dev)
+    if a.kind == "spmm":
+        X = torch.rand(A.n_cols, a.k, device=dev, dtype=D.vec_dtype)
+        Y = torch.empty(A.n_rows, a.k, device=dev, dtype=D.vec_dtype)
+        run = lambda: batch.spmm(D, X, Y)  # noqa: E731
+    else:
+        x = torch.from_numpy(synth.vector(A.n_cols, seed=a.seed)).to(dev, D.vec_dtype)
+        y = torch.empty(A.n_rows, device=dev, dtype=D.vec_dtype)
+        if a.kind == "ellr":
+            run = lambda: pjds.ellr_spmv(D, x, y)  # noqa: E731
+        else:
+            kw = dict(staged=1 if a.staged else 0, threads_per_row=a.threads_per_row,
+                      rows_per_thread=a.rows_per_thread)
+            run = lambda: pjds.pjds_spmv_cfg(D, x, y, **kw)  # noqa: E731
+    for _ in range(a.warmup):
+        run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    status = pjds.pjds_device_status() if a.staged else 0
+    print(json.dumps({"matrix": a.matrix, "n_rows": A.n_rows, "nnz": A.nnz, "dtype": a.dtype, "kind": a.kind,
+                      "permuted": a.permuted, "staged": a.staged, "us": [round(t, 2) for t in times],
+                      "device_status": status}))
+    return 0 if status == 0 else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())
