@@ -58,3 +58,18 @@ def test_model_json_roundtrip(L, tmp_path):
     L.save(m, str(p), {"note": "test"})
     m2 = L.load(str(p))
     assert np.array_equal(np.array(m.w2), np.array(m2.w2)) and m.b3 == m2.b3
+
+
+def test_committed_model_and_data_are_consistent(L):
+    import json
+    import os
+    here = os.path.dirname(L.MODEL_PATH)
+    m = L.load()
+    assert len(m.w1) == 64 * 13 and len(m.w2) == 64 * 64 and m.out_std > 0
+    meta = json.load(open(L.MODEL_PATH))["meta"]
+    for d in ("f64", "f32", "bf16"):
+        assert meta["heldout"][d]["mean_regret"] <= 0.05
+    data = np.load(os.path.join(here, "data", "tuner_timings_gb300.npz"))
+    assert data["features"].shape == (2200, 8) and data["times_us"].shape == (2200, 48)
+    assert int(data["n_train"]) == 2000
+    assert np.isfinite(data["times_us"]).mean() > 0.99
