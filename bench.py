@@ -43,19 +43,20 @@ L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes per launch of the timed pJDS kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload; valid only
-# while the kernel sources hash to the recorded value.
+# while the kernel's source (spmv_kernels.cuh) hashes to the recorded value and
+# the launch configuration is the recorded one.
 NCU_TRAFFIC = {
     # profiles/pjds_rows_kernel_hmep6.2M_f64.md: 1.62 GB read + 161 MB write per launch
-    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_781_000_000, "src": "bc3cf561b6fbec2a"},
+    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_781_000_000, "src": "81997970780652d8",
+                                   "cfg": {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128,
+                                           "unroll": 4, "staged": 0}},
 }
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1112_5588_gb300", "csrc")
-    for name in ("spmv_kernels.cuh", "spmv_launch.cuh", "api.cu"):
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_1112_5588_gb300", "csrc", "spmv_kernels.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -322,8 +323,9 @@ def run_ours(args, world, rank, local_rank):
             prec_gpu = precision_oracle_checks(oracle, prec_gpu)
 
     src_hash = kernel_source_hash()
+    launched = pjds.pjds_spmv_resolve(D)
     tr = NCU_TRAFFIC.get(("hmep_f64_pjds", A.n_rows))
-    traffic = tr["bytes"] if tr and tr["src"] == src_hash else None
+    traffic = tr["bytes"] if tr and tr["src"] == src_hash and tr["cfg"] == launched else None
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(per_launch * 1e3, 5), "higher_is_better": True,
@@ -343,6 +345,7 @@ def run_ours(args, world, rank, local_rank):
         "error_fp64_normwise": err,
         "setup_s": {"generate": round(t_gen, 2), "pjds_create": round(t_conv, 2)},
         "kernel_src": src_hash,
+        "kernel_cfg": launched,
         **side,
         "precision": prec_gpu["report"] if prec_gpu else None,
     }
