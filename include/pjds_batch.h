@@ -39,15 +39,19 @@ typedef struct pjds_batch pjds_batch;
 
 /*
  * Device bytes of the plan for these matrices: a work counter, one
- * descriptor per matrix and one entry per tile of 256 sorted rows.
+ * descriptor per matrix and room for one entry per tile (an upper bound:
+ * tiles hold 256 sorted rows, or 32 rows whose block has 64 or more entries,
+ * each such row then shared by 8 lanes).
  */
 int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes);
 
 /*
  * Build a plan for y_m = A_m x_m, m < n_mats. mats[m] are device views of
  * pJDS matrices of one dtype (original or permuted basis each); xs[m], ys[m]
- * their device vectors. The tiles of all matrices are ordered by their
- * stored work, largest first, and copied into plan_dev (caller-owned device
+ * their device vectors. Each matrix is cut into tiles of sorted rows: 32
+ * rows with 8 lanes per row while the rows' block has 64 or more entries,
+ * then 256 rows with one thread per row. The tiles of all matrices are
+ * ordered by their stored work per lane, largest first, and copied into plan_dev (caller-owned device
  * memory of pjds_batch_plan_bytes). Reads each matrix's block lengths back
  * to the host once. *out receives a host handle (free with
  * pjds_batch_destroy). Errors: PJDS_EINVAL (mixed dtypes, sizes), ENOMEM,

@@ -138,11 +138,52 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int6
   return acc;
 }
 
-// CTAs take tiles (matrix, first sorted row) from a work counter until none
-// is left; a tile's rows are one per thread. No CTA ever waits for another.
+// LANES consecutive lanes share sorted row i: lane s takes jagged diagonals
+// s, s + LANES, ...; the partial sums are added with shuffles (fixed tree).
+template <typename TV, typename TX, typename IDX, int LANES>
+__device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d, int64_t i, int32_t s, bool active) {
+  using TA = typename dev::Acc<TV>::T;
+  constexpr int U = 4;
+  const TV *__restrict__ val = static_cast<const TV *>(d.val);
+  const TX *__restrict__ x = static_cast<const TX *>(d.x);
+  const int32_t L = active ? __ldg(d.block_len + (int32_t)(i / d.b)) : 0;
+  TA acc = TA(0);
+  for (int32_t j = s; j < L; j += U * LANES) {
+    int32_t c[U];
+    TV v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u * LANES < L) {
+        const IDX o = (IDX)__ldg(d.col_start + j + u * LANES) + (IDX)i;
+        c[u] = __ldcs(d.col + o);
+        v[u] = dev::ld_stream1(val + o);
+      } else {
+        c[u] = -1;
+        v[u] = TV{};
+      }
+    }
+    TX xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = dev::gather(x, c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
+  }
+#pragma unroll
+  for (int off = LANES / 2; off >= 1; off /= 2) acc += __shfl_down_sync(0xffffffffu, acc, off, LANES);
+  return acc;
+}
+
+constexpr int LONG_LANES = 8;     // lanes per row in tiles of long rows
+constexpr int LONG_ROWS = BT / LONG_LANES;
+constexpr int LONG_MIN_LEN = 64;  // block length from which rows get LONG_LANES lanes
+
+// CTAs take tiles (matrix, first sorted row, rows, lanes per row) from a work
+// counter until none is left: short-row tiles have one row per thread,
+// long-row tiles LONG_ROWS rows with LONG_LANES lanes each. No CTA ever waits
+// for another.
 template <typename TV, typename TX>
 __global__ void __launch_bounds__(BT)
-    batch_kernel(const Desc *__restrict__ descs, const int2 *__restrict__ tiles, int32_t n_tiles,
+    batch_kernel(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
                  int32_t *__restrict__ counter) {
   __shared__ int32_t s_tile;
   for (;;) {
@@ -151,13 +192,22 @@ __global__ void __launch_bounds__(BT)
     const int32_t t = s_tile;
     __syncthreads();
     if (t >= n_tiles) return;
-    const int2 tl = tiles[t];
+    const int4 tl = tiles[t];
     const Desc d = descs[tl.x];
-    const int64_t i = (int64_t)tl.y + threadIdx.x;
-    if (i < d.n_rows) {
-      const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
-      TX *y = static_cast<TX *>(d.y);
-      y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
+    TX *y = static_cast<TX *>(d.y);
+    if (tl.w == 1) {
+      const int64_t i = (int64_t)tl.y + threadIdx.x;
+      if ((int32_t)threadIdx.x < tl.z && i < d.n_rows) {
+        const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
+        y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
+      }
+    } else {  // the whole CTA stays for the shuffles
+      const int32_t r = threadIdx.x / LONG_LANES, s = threadIdx.x % LONG_LANES;
+      const int64_t i = (int64_t)tl.y + r;
+      const bool active = r < tl.z && i < d.n_rows;
+      const auto acc = d.idx64 ? desc_row_lanes<TV, TX, int64_t, LONG_LANES>(d, i, s, active)
+                               : desc_row_lanes<TV, TX, int32_t, LONG_LANES>(d, i, s, active);
+      if (active && s == 0) y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
     }
   }
 }
@@ -174,7 +224,7 @@ struct pjds_batch {
   int32_t dtype, n_mats, n_tiles, n_ctas;
   int32_t *counter;
   const Desc *descs;
-  const int2 *tiles;
+  const int4 *tiles;
   cudaGraphExec_t exec;
 };
 
@@ -238,14 +288,15 @@ extern "C" int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, v
 
 // ----------------------------------------------------------------------------- batch
 
-static int64_t tiles_of(const pjds_dev &A) { return ((int64_t)A.n_rows + BT - 1) / BT; }
+// upper bound of a matrix's tiles (every tile a long-row tile)
+static int64_t tiles_of(const pjds_dev &A) { return ((int64_t)A.n_rows + LONG_ROWS - 1) / LONG_ROWS; }
 
 extern "C" int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes) {
   clear_error();
   if (n_mats <= 0 || !mats || !bytes) return set_error(PJDS_EINVAL, "bad arguments");
   int64_t nt = 0;
   for (int32_t m = 0; m < n_mats; ++m) nt += tiles_of(mats[m]);
-  *bytes = a256(sizeof(int32_t)) + a256(sizeof(Desc) * (size_t)n_mats) + a256(sizeof(int2) * (size_t)nt);
+  *bytes = a256(sizeof(int32_t)) + a256(sizeof(Desc) * (size_t)n_mats) + a256(sizeof(int4) * (size_t)nt);
   return PJDS_OK;
 }
 
@@ -263,7 +314,7 @@ extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const voi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<Desc> descs((size_t)n_mats);
   struct T {
-    int32_t m, row0;
+    int32_t m, row0, rows, lanes;
     int64_t cost;
   };
   std::vector<T> tiles;
@@ -294,22 +345,32 @@ extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const voi
     cudaError_t e = cudaMemcpyAsync(bl.data(), A.block_len, sizeof(int32_t) * bl.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(PJDS_ECUDA, "read block lengths: %s", cudaGetErrorString(e));
-    for (int64_t t0 = 0; t0 < A.n_rows; t0 += BT) {
+    // long-row tiles first (blocks are sorted by length), then short-row tiles
+    for (int64_t t0 = 0; t0 < A.n_rows;) {
+      const int64_t L = bl[(size_t)(t0 / A.b)];
+      const bool lng = L >= LONG_MIN_LEN;
+      const int64_t rows = std::min<int64_t>(lng ? LONG_ROWS : BT, A.n_rows - t0);
+      // work estimate: stored entries of the tile's rows over the lanes per row
       int64_t cost = 0;
-      for (int64_t r = t0; r < std::min<int64_t>(t0 + BT, A.n_pad); r += A.b) cost += (int64_t)bl[(size_t)(r / A.b)];
-      tiles.push_back(T{m, (int32_t)t0, cost});
+      for (int64_t r = t0; r < t0 + rows;) {
+        const int64_t blk = r / A.b, end = std::min<int64_t>((blk + 1) * A.b, t0 + rows);
+        cost += (end - r) * (int64_t)bl[(size_t)blk];
+        r = end;
+      }
+      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, lng ? LONG_LANES : 1, lng ? cost / LONG_LANES : cost});
+      t0 += rows;
     }
   }
   std::stable_sort(tiles.begin(), tiles.end(), [](const T &a, const T &b) { return a.cost > b.cost; });
-  std::vector<int2> tl(tiles.size());
-  for (size_t i = 0; i < tiles.size(); ++i) tl[i] = make_int2(tiles[i].m, tiles[i].row0);
+  std::vector<int4> tl(tiles.size());
+  for (size_t i = 0; i < tiles.size(); ++i) tl[i] = make_int4(tiles[i].m, tiles[i].row0, tiles[i].rows, tiles[i].lanes);
   char *p = static_cast<char *>(plan_dev);
   int32_t *counter = reinterpret_cast<int32_t *>(p);
   Desc *dd = reinterpret_cast<Desc *>(p + a256(sizeof(int32_t)));
-  int2 *td = reinterpret_cast<int2 *>(p + a256(sizeof(int32_t)) + a256(sizeof(Desc) * (size_t)n_mats));
+  int4 *td = reinterpret_cast<int4 *>(p + a256(sizeof(int32_t)) + a256(sizeof(Desc) * (size_t)n_mats));
   cudaError_t e = cudaMemcpyAsync(dd, descs.data(), sizeof(Desc) * descs.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !tl.empty())
-    e = cudaMemcpyAsync(td, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(td, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_error(PJDS_ECUDA, "upload plan: %s", cudaGetErrorString(e));
   int dev = 0, sms = 0, per_sm = 0;
