@@ -95,3 +95,76 @@ def test_stencil_bf16_full(P, oracle_lib, stencil):
     xd = x32.astype(np.float64)
     r = parity.check_fp32(y, oracle_lib.crs_spmv(Ar, xd), oracle_lib.crs_absmv(Ar, xd), np.diff(stencil.row_ptr))
     assert r["ok"], r
+
+
+@pytest.mark.parametrize("lo,max_outer,inner", [("f32", 6, 50), ("bf16", 12, 25)])
+def test_stencil_cg_refined_full(P, oracle_lib, stencil, lo, max_outer, inner):
+    # the 300-step refined CG of the precision workload at full size: the fp64
+    # residual of the returned solution, evaluated by the oracle, is <= 1e-12
+    import torch
+    from paper_1112_5588_gb300 import krylov
+    A = stencil
+    H64 = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64", permute_cols=True)
+    perm = H64.perm.copy()
+    D64 = H64.to_device("cuda")
+    H64.destroy()
+    Dlo = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=lo, permute_cols=True).to_device("cuda")
+    b = synth.vector(A.n_rows, seed=1235)
+    bp = torch.from_numpy(b[perm]).cuda()
+    xp = torch.zeros_like(bp)
+    res = krylov.cg_solve(D64, Dlo, bp, xp, max_outer=max_outer, inner_iters=inner)
+    x = np.empty(A.n_rows)
+    x[perm] = xp.cpu().numpy()
+    rel = np.linalg.norm(b - oracle_lib.crs_spmv(A, x)) / np.linalg.norm(b)
+    assert rel <= 1e-12, (rel, res)
+    assert res["inner_total"] == 300
+
+
+def test_dlr_spmm_k32_full(P, oracle_lib):
+    # block product of the batching workload at full size: DLR-like N = 280k,
+    # 144 nonzeros per row, fp32, k = 32
+    import torch
+    from paper_1112_5588_gb300 import batch
+    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=1234)
+    k = 32
+    X = np.random.default_rng(3).uniform(-1, 1, (A.n_cols, k)).astype(np.float32)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f32")
+    D = H.to_device("cuda")
+    Xt = torch.from_numpy(X).cuda()
+    Yt = torch.empty(A.n_rows, k, device="cuda")
+    batch.spmm(D, Xt, Yt)
+    torch.cuda.synchronize()
+    Ar = A._replace(val=oracle_lib.round_f32(A.val))
+    Xd = X.astype(np.float64)
+    Yr = oracle_lib.crs_spmm(Ar, Xd)
+    S = oracle_lib.crs_spmm(Ar._replace(val=np.abs(Ar.val)), np.abs(Xd))
+    Y = Yt.double().cpu().numpy()
+    lens = np.diff(A.row_ptr)
+    for c in range(k):
+        r = parity.check_fp32(Y[:, c], Yr[:, c], S[:, c], lens)
+        assert r["ok"], (c, r)
+
+
+def test_batch_64_uneven_full(P, oracle_lib):
+    # the 64-matrix batch of the batching workload (N log-uniform in [10k, 500k],
+    # Zipf(2) rows capped at 512, fp64), one persistent graph launch
+    import torch
+    from paper_1112_5588_gb300 import batch
+    rng = np.random.default_rng(1234)
+    sizes = np.exp(rng.uniform(np.log(10_000), np.log(500_000), 64)).astype(int)
+    mats, devs, xs, ys = [], [], [], []
+    for m, n in enumerate(sizes):
+        M = synth.zipf_rows(int(n), s=2.0, len_max=512, seed=1234 + m)
+        devs.append(P.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32).to_device("cuda"))
+        xs.append(torch.from_numpy(synth.vector(M.n_cols, seed=m)).cuda())
+        ys.append(torch.full((M.n_rows,), float("nan"), dtype=torch.float64, device="cuda"))
+        mats.append(M)
+    B = batch.Batch(devs, xs, ys)
+    B.run(use_graph=True)
+    torch.cuda.synchronize()
+    for M, x, y in zip(mats, xs, ys):
+        xh = x.cpu().numpy()
+        r = parity.check_fp64(y.cpu().numpy(), oracle_lib.crs_spmv(M, xh), oracle_lib.crs_absmv(M, xh),
+                              np.diff(M.row_ptr))
+        assert r["ok"], r
+    B.destroy()
