@@ -49,7 +49,7 @@ NCU_TRAFFIC = {
     # profiles/pjds_rows_kernel_hmep6.2M_f64.md: 1.62 GB read + 161 MB write per launch
     ("hmep_f64_pjds", 6_200_000): {"bytes": 1_781_000_000, "src": "81997970780652d8",
                                    "cfg": {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128,
-                                           "unroll": 4, "staged": 0}},
+                                           "unroll": 4, "staged": 0, "index64": 0}},
 }
 
 

@@ -165,7 +165,9 @@ typedef struct pjds_launch {
   int32_t block_threads;
   int32_t unroll;
   int32_t staged;
-  int32_t reserved[3];
+  int32_t index64;  /* 1: 64-bit element offsets even when 32 bits suffice (they are
+                       used automatically from 2^31 stored entries on) */
+  int32_t reserved[2];
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);

@@ -74,6 +74,7 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   c.block_threads = A->dtype == PJDS_F32 ? 256 : 128;
   c.unroll = 0;  // filled in by check_cfg once R and T are final
   c.staged = 0;
+  c.index64 = 0;
   return c;
 }
 
@@ -102,6 +103,7 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->threads_per_row > 1 && !cfg->rows_per_thread) c.rows_per_thread = 1;
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
     if (cfg->unroll) c.unroll = cfg->unroll;
+    if (cfg->index64) c.index64 = 1;
     if (cfg->staged) {
       c.staged = 1;
       if (!cfg->rows_per_thread) c.rows_per_thread = 1;
@@ -124,7 +126,8 @@ extern "C" int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds
   out->block_threads = c.block_threads;
   out->unroll = c.unroll;
   out->staged = c.staged;
-  out->reserved[0] = out->reserved[1] = out->reserved[2] = 0;
+  out->index64 = c.index64;
+  out->reserved[0] = out->reserved[1] = 0;
   return PJDS_OK;
 }
 

@@ -16,6 +16,7 @@ struct LaunchCfg {
   int block_threads;    // CTA size
   int unroll;           // U: jagged diagonals per chunk of the j-loop
   int staged;           // 1: bulk-copy staged persistent kernel (R = T = 1)
+  int index64;          // 1: 64-bit element offsets regardless of size
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -92,7 +93,7 @@ template <typename TV, typename TX>
 int launch_pjds(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s) {
   const TX *xx = static_cast<const TX *>(x);
   TX *yy = static_cast<TX *>(y);
-  const bool small = A->n_stored + A->n_pad < 0x7fffffffLL;
+  const bool small = A->n_stored + A->n_pad < 0x7fffffffLL && !c.index64;
   const bool scatter = !A->permute_cols;
   if (small)
     return scatter ? launch_pjds_idx<TV, TX, int32_t, true>(A, xx, yy, c, s)

@@ -53,7 +53,7 @@ class _PjdsDevS(ctypes.Structure):
 
 class _LaunchS(ctypes.Structure):
     _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32),
-                ("staged", _i32), ("reserved", _i32 * 3)]
+                ("staged", _i32), ("index64", _i32), ("reserved", _i32 * 2)]
 
 
 class _EllrHostS(ctypes.Structure):
@@ -258,26 +258,27 @@ def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> t
 
 def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
                   threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, staged: int = 0,
-                  stream=None) -> torch.Tensor:
+                  index64: int = 0, stream=None) -> torch.Tensor:
     """y = A x with an explicit kernel configuration (pjds_spmv_cfg)."""
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y
 
 
 def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, block_threads: int = 0,
-                      unroll: int = 0, staged: int = 0) -> dict:
+                      unroll: int = 0, staged: int = 0, index64: int = 0) -> dict:
     """The launch configuration pjds_spmv_cfg would use (no launch). `A` is a
     PjdsDevice or a PjdsHost (only sizes and alignment are read)."""
     s = A.struct if isinstance(A, PjdsDevice) else _dev_struct_from_host(A)
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64)
     out = _LaunchS()
     _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
-            "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged}
+            "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged,
+            "index64": out.index64}
 
 
 def pjds_wait_selftest(which: int = 0, stream=None) -> None:

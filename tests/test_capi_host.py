@@ -192,7 +192,7 @@ def test_resolve_defaults(P):
     A = synth.hmep_like(n=10_000, seed=1)
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
     assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128, "unroll": 4,
-                                      "staged": 0}
+                                      "staged": 0, "index64": 0}
     Z = synth.zipf_rows(10_000, s=2.0, len_max=512, seed=1)
     HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
     assert P.pjds_spmv_resolve(HZ)["threads_per_row"] == 2

@@ -75,7 +75,7 @@ CONFIGS = [
     dict(threads_per_row=2), dict(threads_per_row=4), dict(threads_per_row=8, block_threads=512),
     dict(threads_per_row=1, unroll=4), dict(threads_per_row=1, unroll=16), dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=2, unroll=2),
     dict(rows_per_thread=4, unroll=4), dict(threads_per_row=4, unroll=2), dict(threads_per_row=2, block_threads=32),
-    dict(staged=1),
+    dict(staged=1), dict(index64=1), dict(threads_per_row=4, index64=1), dict(rows_per_thread=2, index64=1),
 ]
 CONFIG_SHAPES = [SHAPES[1], SHAPES[4], SHAPES[6]]
 
@@ -108,7 +108,8 @@ def test_rows_per_thread_bit_identical_to_one_row(P):
     x = synth.vector(A.n_cols, seed=9)
     y1, _, _ = run_pjds(P, A, x, cfg=dict(rows_per_thread=1, threads_per_row=1))
     for cfg in (dict(rows_per_thread=2), dict(rows_per_thread=4), dict(threads_per_row=1, unroll=8),
-                dict(threads_per_row=1, unroll=16), dict(staged=1),
+                dict(threads_per_row=1, unroll=16), dict(staged=1), dict(threads_per_row=1, index64=1),
+                dict(rows_per_thread=4, index64=1), dict(staged=1, index64=1),
                 dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=4, unroll=4)):
         yR, _, _ = run_pjds(P, A, x, cfg=cfg)
         assert np.array_equal(y1.view(np.uint64), yR.view(np.uint64)), cfg
