@@ -7,8 +7,10 @@
 // read by the kernels that need them, so a run of inner iterations has no
 // host round trip and can be captured once in a CUDA graph. Inner products
 // accumulate in fp64 with a fixed reduction order: per-CTA partial sums
-// (warp shuffles, then one warp) into the workspace, then one CTA adds the
-// partials in a fixed pattern — results are bitwise reproducible.
+// (warp shuffles, then one warp) into the workspace; the CTA that finishes
+// last (a counter in the workspace) adds the partials in index order and
+// applies the scalar update, inside the same launch. The summation pattern
+// does not depend on which CTA is last — results are bitwise reproducible.
 #include <float.h>
 #include <math.h>
 #include <string.h>
@@ -24,11 +26,12 @@
 namespace pjds {
 namespace kry {
 
-constexpr int KT = 256;      // threads per CTA of the vector and product kernels
-constexpr int FIN_T = 1024;  // threads of the one-CTA finalisation
+constexpr int KT = 256;  // threads per CTA of the vector and product kernels
 
 // slots of the device scalar block
-enum { S_RR = 0, S_PQ, S_ALPHA, S_BETA, S_NRM, S_INVNRM, S_AUX0, S_AUX1, S_AUX2, S_COUNT = 16 };
+// (slot S_CTR holds the 32-bit arrival counter of the reduction in flight; it
+// is 0 between launches)
+enum { S_RR = 0, S_PQ, S_ALPHA, S_BETA, S_NRM, S_INVNRM, S_AUX0, S_AUX1, S_AUX2, S_CTR = 15, S_COUNT = 16 };
 // finalisation operations
 enum { F_ALPHA = 0, F_BETA, F_RR, F_NORM, F_LALPHA, F_LBETA, F_STORE };
 
@@ -44,6 +47,77 @@ __device__ __forceinline__ double block_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   }
   return s;  // complete in thread 0
+}
+
+// Where a reduction's result goes: the partial-sum array (one slot per CTA),
+// the scalar block (its S_CTR slot is the arrival counter) and the update.
+struct Fin {
+  double *partial;
+  double *scal;
+  double *out;
+  int32_t op, j;
+};
+
+// The scalar update `op` with the complete sum v.
+__device__ __forceinline__ void apply_op(double v, const Fin &f) {
+  double *scal = f.scal;
+  switch (f.op) {
+    case F_ALPHA:  // alpha = (r, r) / (p, A p)
+      scal[S_PQ] = v;
+      scal[S_ALPHA] = v != 0.0 ? scal[S_RR] / v : 0.0;
+      break;
+    case F_BETA:  // beta = (r', r') / (r, r)
+      scal[S_BETA] = scal[S_RR] != 0.0 ? v / scal[S_RR] : 0.0;
+      scal[S_RR] = v;
+      break;
+    case F_RR:
+      scal[S_RR] = v;
+      break;
+    case F_NORM: {
+      const double nrm = sqrt(v);
+      scal[S_NRM] = nrm;
+      scal[S_INVNRM] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      break;
+    }
+    case F_LALPHA:
+      f.out[f.j] = v;
+      break;
+    case F_LBETA: {
+      const double nrm = sqrt(v);
+      f.out[f.j] = nrm;
+      scal[S_INVNRM] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      break;
+    }
+    default:  // F_STORE
+      scal[f.j] = v;
+      break;
+  }
+}
+
+// End of a reducing kernel, called by every thread; thread 0 holds the CTA's
+// sum s. The sum goes to partial[blockIdx.x], is made visible device-wide,
+// and the CTA counts itself in. The CTA that arrives last adds all gridDim.x
+// partials in index order (strided per thread, then the CTA tree: the same
+// pattern whichever CTA it is), applies the update and puts the counter back
+// to 0 for the next reduction on the stream.
+__device__ __forceinline__ void finish(double s, const Fin &f) {
+  __shared__ int last;
+  unsigned *ctr = reinterpret_cast<unsigned *>(f.scal + S_CTR);
+  if (threadIdx.x == 0) {
+    f.partial[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (uint32_t k = threadIdx.x; k < gridDim.x; k += KT) v += __ldcg(f.partial + k);
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    apply_op(v, f);
+    *ctr = 0u;
+  }
 }
 
 // One sorted row's product in the permuted basis (Listing 2 with the loop
@@ -79,104 +153,67 @@ __device__ __forceinline__ typename dev::Acc<TV>::T row_product(const TV *__rest
   return acc;
 }
 
-// MODE 0: y = A x and partial = sum x_i y_i.  MODE 1: y = bv - A x and
-// partial = sum y_i^2 (the fp64 residual of the refinement loop).
+// The reducing kernels below run a grid of at most as many CTAs as fit on the
+// GPU at once and stride over the vectors (element i is taken by thread
+// i mod KT of CTA (i / KT) mod gridDim.x); each thread accumulates its own
+// elements in order, so the sum depends only on the grid size, which the host
+// derives from the device and the kernel alone.
+
+// MODE 0: y = A x and the reduction of sum x_i y_i.  MODE 1: y = bv - A x and
+// the reduction of sum y_i^2 (the fp64 residual of the refinement loop). The
+// value array arrives untyped so that every instance for one vector type has
+// the same signature.
 template <typename TV, typename TX, typename IDX, int MODE>
 __global__ void __launch_bounds__(KT)
-    spmv_dot_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ col_start,
-                    const int32_t *__restrict__ block_len, const TX *__restrict__ x, TX *__restrict__ y,
-                    const TX *__restrict__ bv, double *__restrict__ partial, int32_t n_rows, int32_t b) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+    spmv_dot_kernel(const void *__restrict__ val_, const int32_t *__restrict__ col,
+                    const int64_t *__restrict__ col_start, const int32_t *__restrict__ block_len,
+                    const TX *__restrict__ x, TX *__restrict__ y, const TX *__restrict__ bv, Fin f, int32_t n_rows,
+                    int32_t b) {
+  const TV *__restrict__ val = static_cast<const TV *>(val_);
   double contrib = 0.0;
-  if (i < n_rows) {
+  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n_rows; i += (int64_t)gridDim.x * KT) {
     const int32_t L = __ldg(block_len + (int32_t)(i / b));
     const auto acc = row_product<TV, TX, IDX>(val, col, col_start, L, i, x);
     TX yi;
     if constexpr (MODE == 0) {
       yi = (TX)acc;
-      contrib = (double)x[i] * (double)yi;
+      contrib += (double)x[i] * (double)yi;
     } else {
       yi = (TX)((double)bv[i] - (double)acc);
-      contrib = (double)yi * (double)yi;
+      contrib += (double)yi * (double)yi;
     }
     y[i] = yi;
   }
   const double s = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-// Fixed-order sum of nb partials, then the scalar update `op`.
-__global__ void __launch_bounds__(FIN_T)
-    finalize_kernel(const double *__restrict__ partial, int32_t nb, double *__restrict__ scal, int32_t op,
-                    double *__restrict__ out, int32_t j) {
-  __shared__ double sh[FIN_T / 32];
-  double v = 0.0;
-  for (int32_t k = threadIdx.x; k < nb; k += FIN_T) v += partial[k];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  if (w != 0) return;
-  v = l < FIN_T / 32 ? sh[l] : 0.0;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (l != 0) return;
-  switch (op) {
-    case F_ALPHA:  // alpha = (r, r) / (p, A p)
-      scal[S_PQ] = v;
-      scal[S_ALPHA] = v != 0.0 ? scal[S_RR] / v : 0.0;
-      break;
-    case F_BETA:  // beta = (r', r') / (r, r)
-      scal[S_BETA] = scal[S_RR] != 0.0 ? v / scal[S_RR] : 0.0;
-      scal[S_RR] = v;
-      break;
-    case F_RR:
-      scal[S_RR] = v;
-      break;
-    case F_NORM: {
-      const double nrm = sqrt(v);
-      scal[S_NRM] = nrm;
-      scal[S_INVNRM] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-      break;
-    }
-    case F_LALPHA:
-      out[j] = v;
-      break;
-    case F_LBETA: {
-      const double nrm = sqrt(v);
-      out[j] = nrm;
-      scal[S_INVNRM] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-      break;
-    }
-    default:  // F_STORE
-      scal[j] = v;
-      break;
-  }
+  finish(s, f);
 }
 
 template <typename TX>
-__global__ void __launch_bounds__(KT) sumsq_kernel(const TX *__restrict__ v, double *__restrict__ partial, int32_t n) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
-  const double x = i < n ? (double)v[i] : 0.0;
-  const double s = block_sum(x * x);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+__global__ void __launch_bounds__(KT) sumsq_kernel(const TX *__restrict__ v, Fin f, int32_t n) {
+  double contrib = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
+    const double x = (double)v[i];
+    contrib += x * x;
+  }
+  const double s = block_sum(contrib);
+  finish(s, f);
 }
 
-// d += alpha p; r -= alpha q; partial = sum r_i^2
+// d += alpha p; r -= alpha q; reduces sum r_i^2
 template <typename TX>
 __global__ void __launch_bounds__(KT)
     cg_update_kernel(TX *__restrict__ d, TX *__restrict__ r, const TX *__restrict__ p, const TX *__restrict__ q,
-                     const double *__restrict__ scal, double *__restrict__ partial, int32_t n) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+                     Fin f, int32_t n) {
+  const TX a = (TX)f.scal[S_ALPHA];
   double contrib = 0.0;
-  if (i < n) {
-    const TX a = (TX)scal[S_ALPHA];
+  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
     d[i] = d[i] + a * p[i];
     const TX ri = r[i] - a * q[i];
     r[i] = ri;
-    contrib = (double)ri * (double)ri;
+    contrib += (double)ri * (double)ri;
   }
   const double s = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  finish(s, f);
 }
 
 // p = r + beta p
@@ -188,22 +225,22 @@ __global__ void __launch_bounds__(KT)
 }
 
 // Start of an inner solve: r = p = (r64 / ||r64||) in the inner type, d = 0,
-// partial = sum r_i^2.
+// reduces sum r_i^2.
 template <typename TL>
 __global__ void __launch_bounds__(KT)
     ir_start_kernel(const double *__restrict__ r64, TL *__restrict__ r, TL *__restrict__ p, TL *__restrict__ d,
-                    const double *__restrict__ scal, double *__restrict__ partial, int32_t n) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+                    Fin f, int32_t n) {
+  const double inv = f.scal[S_INVNRM];
   double contrib = 0.0;
-  if (i < n) {
-    const TL ri = (TL)(r64[i] * scal[S_INVNRM]);
+  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
+    const TL ri = (TL)(r64[i] * inv);
     r[i] = ri;
     p[i] = ri;
     d[i] = TL(0);
-    contrib = (double)ri * (double)ri;
+    contrib += (double)ri * (double)ri;
   }
   const double s = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  finish(s, f);
 }
 
 // x += ||r64|| d (fp64)
@@ -226,22 +263,22 @@ __global__ void __launch_bounds__(KT)
   }
 }
 
-// w = w - alpha_j v - beta_j vprev (in fp64, stored in TX); partial = sum w_i^2
+// w = w - alpha_j v - beta_j vprev (in fp64, stored in TX); reduces sum w_i^2
 template <typename TX>
 __global__ void __launch_bounds__(KT)
     lanczos_orth_kernel(TX *__restrict__ w, const TX *__restrict__ v, const TX *__restrict__ vprev,
-                        const double *__restrict__ alpha, const double *__restrict__ beta, int32_t j,
-                        double *__restrict__ partial, int32_t n) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+                        const double *__restrict__ alpha, const double *__restrict__ beta, int32_t j, Fin f,
+                        int32_t n) {
+  const double aj = alpha[j], bj = beta[j];
   double contrib = 0.0;
-  if (i < n) {
-    const double wi = (double)w[i] - alpha[j] * (double)v[i] - beta[j] * (double)vprev[i];
+  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
+    const double wi = (double)w[i] - aj * (double)v[i] - bj * (double)vprev[i];
     const TX ws = (TX)wi;
     w[i] = ws;
-    contrib = (double)ws * (double)ws;
+    contrib += (double)ws * (double)ws;
   }
   const double s = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  finish(s, f);
 }
 
 // basis_row = v (optional); vprev = v; v = w / beta_{j+1}
@@ -258,36 +295,33 @@ __global__ void __launch_bounds__(KT)
   }
 }
 
-// y = sum_j s_j basis[j] (fp64); partial = sum y_i^2
+// y = sum_j s_j basis[j] (fp64); reduces sum y_i^2
 template <typename TB>
 __global__ void __launch_bounds__(KT)
     ritz_combine_kernel(const TB *__restrict__ basis, const double *__restrict__ s, int32_t k, int32_t n,
-                        double *__restrict__ y, double *__restrict__ partial) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+                        double *__restrict__ y, Fin f) {
   double contrib = 0.0;
-  if (i < n) {
+  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
     double acc = 0.0;
     for (int32_t j = 0; j < k; ++j) acc = fma(s[j], (double)__ldcs(basis + (int64_t)j * n + i), acc);
     y[i] = acc;
-    contrib = acc * acc;
+    contrib += acc * acc;
   }
   const double sm = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = sm;
+  finish(sm, f);
 }
 
-// partial = sum (w_i - theta y_i)^2 with theta = scal[S_AUX1] / scal[S_AUX0]
+// reduces sum (w_i - theta y_i)^2 with theta = scal[S_AUX1] / scal[S_AUX0]
 __global__ void __launch_bounds__(KT)
-    ritz_residual_kernel(const double *__restrict__ w, const double *__restrict__ y, const double *__restrict__ scal,
-                         double *__restrict__ partial, int32_t n) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+    ritz_residual_kernel(const double *__restrict__ w, const double *__restrict__ y, Fin f, int32_t n) {
+  const double theta = f.scal[S_AUX1] / f.scal[S_AUX0];
   double contrib = 0.0;
-  if (i < n) {
-    const double theta = scal[S_AUX1] / scal[S_AUX0];
+  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
     const double e = w[i] - theta * y[i];
-    contrib = e * e;
+    contrib += e * e;
   }
   const double s = block_sum(contrib);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  finish(s, f);
 }
 
 // ----------------------------------------------------------------------------- host helpers
@@ -350,35 +384,64 @@ static int check_square_permuted(const pjds_dev *A, const char *name) {
   return PJDS_OK;
 }
 
-// product kernels dispatched on value type and index width
+// CTAs of a reducing kernel: as many as are resident on all SMs at once at
+// the kernel's occupancy (the grid-stride loops cover the rest), at most one
+// per KT elements. Queried outside any stream capture.
+template <typename K>
+static int red_grid(K kernel, int32_t n, int32_t *grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, KT, 0);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+  if (sms < 1 || per_sm < 1) return set_error(PJDS_ECUDA, "kernel does not fit on an SM");
+  *grid = (int32_t)std::min<int64_t>(std::max<int32_t>(n_blocks_of(n), 1), (int64_t)sms * per_sm);
+  return PJDS_OK;
+}
+
+// A product-and-reduce kernel chosen by value type and index width, with its
+// grid.
+template <typename TX, int MODE>
+struct Dot {
+  void (*fn)(const void *, const int32_t *, const int64_t *, const int32_t *, const TX *, TX *, const TX *, Fin,
+             int32_t, int32_t);
+  int32_t grid;
+};
+
 template <typename TV, typename TX, int MODE>
-static void launch_spmv_dot(const pjds_dev *A, const TX *x, TX *y, const TX *bv, double *partial, cudaStream_t s) {
-  const int32_t nb = n_blocks_of(A->n_rows);
-  const TV *val = static_cast<const TV *>(A->val);
+static int make_dot_typed(const pjds_dev *A, Dot<TX, MODE> *d) {
   if (A->n_stored + A->n_pad < 0x7fffffffLL)
-    spmv_dot_kernel<TV, TX, int32_t, MODE>
-        <<<nb, KT, 0, s>>>(val, A->col, A->col_start, A->block_len, x, y, bv, partial, A->n_rows, A->b);
+    d->fn = spmv_dot_kernel<TV, TX, int32_t, MODE>;
   else
-    spmv_dot_kernel<TV, TX, int64_t, MODE>
-        <<<nb, KT, 0, s>>>(val, A->col, A->col_start, A->block_len, x, y, bv, partial, A->n_rows, A->b);
+    d->fn = spmv_dot_kernel<TV, TX, int64_t, MODE>;
+  return red_grid(d->fn, A->n_rows, &d->grid);
 }
 
-template <typename TX>
-static void spmv_dot_any(const pjds_dev *A, const TX *x, TX *y, double *partial, cudaStream_t s);
+template <typename TX, int MODE>
+static int make_dot(const pjds_dev *A, Dot<TX, MODE> *d);
 template <>
-void spmv_dot_any<double>(const pjds_dev *A, const double *x, double *y, double *partial, cudaStream_t s) {
-  launch_spmv_dot<double, double, 0>(A, x, y, nullptr, partial, s);
+int make_dot<double, 0>(const pjds_dev *A, Dot<double, 0> *d) {
+  return make_dot_typed<double, double, 0>(A, d);
 }
 template <>
-void spmv_dot_any<float>(const pjds_dev *A, const float *x, float *y, double *partial, cudaStream_t s) {
-  if (A->dtype == PJDS_BF16)
-    launch_spmv_dot<dev::bf16_t, float, 0>(A, x, y, nullptr, partial, s);
-  else
-    launch_spmv_dot<float, float, 0>(A, x, y, nullptr, partial, s);
+int make_dot<double, 1>(const pjds_dev *A, Dot<double, 1> *d) {
+  return make_dot_typed<double, double, 1>(A, d);
+}
+template <>
+int make_dot<float, 0>(const pjds_dev *A, Dot<float, 0> *d) {
+  return A->dtype == PJDS_BF16 ? make_dot_typed<dev::bf16_t, float, 0>(A, d) : make_dot_typed<float, float, 0>(A, d);
 }
 
-static void finalize(double *partial, int32_t nb, double *scal, int op, double *out, int32_t j, cudaStream_t s) {
-  finalize_kernel<<<1, FIN_T, 0, s>>>(partial, nb, scal, op, out, j);
+template <typename T>
+struct Same {
+  using type = T;
+};
+
+// (the vector type is taken from the launcher alone)
+template <typename TX, int MODE>
+static void launch_dot(const Dot<TX, MODE> &d, const pjds_dev *A, const typename Same<TX>::type *x,
+                       typename Same<TX>::type *y, const typename Same<TX>::type *bv, const Fin &f, cudaStream_t s) {
+  d.fn<<<d.grid, KT, 0, s>>>(A->val, A->col, A->col_start, A->block_len, x, y, bv, f, A->n_rows, A->b);
 }
 
 // ----------------------------------------------------------------------------- CG
@@ -398,24 +461,31 @@ static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, doubl
   TL *r = cv.take<TL>((size_t)n), *p = cv.take<TL>((size_t)n), *q = cv.take<TL>((size_t)n);
   TL *d = cv.take<TL>((size_t)n);
   double *r64 = cv.take<double>((size_t)n);
+  auto fin = [&](int32_t op, int32_t j) { return Fin{partial, scal, nullptr, op, j}; };
   int rc;
+  Dot<TL, 0> dot_lo;
+  Dot<double, 1> dot_res;
+  int32_t g_sumsq = 0, g_upd = 0, g_start = 0;
+  if ((rc = make_dot(Al, &dot_lo)) || (rc = make_dot(Ah, &dot_res)) || (rc = red_grid(sumsq_kernel<double>, n, &g_sumsq)) ||
+      (rc = red_grid(cg_update_kernel<TL>, n, &g_upd)) || (rc = red_grid(ir_start_kernel<TL>, n, &g_start)))
+    return rc;
 
+  // scalar block and reduction counter start at 0
+  cudaError_t e = cudaMemsetAsync(scal, 0, S_COUNT * sizeof(double), s);
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg: %s", cudaGetErrorString(e));
   // ||b||
-  sumsq_kernel<double><<<nb, KT, 0, s>>>(b, partial, n);
-  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX2, s);
+  sumsq_kernel<double><<<g_sumsq, KT, 0, s>>>(b, fin(F_STORE, S_AUX2), n);
   double bn2 = 0.0;
   if ((rc = launch_check("cg ||b||"))) return rc;
-  cudaError_t e = cudaMemcpyAsync(&bn2, scal + S_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(&bn2, scal + S_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_error(PJDS_ECUDA, "cg: %s", cudaGetErrorString(e));
   const double bnorm = sqrt(bn2);
 
   auto inner_step = [&](cudaStream_t st) {
-    spmv_dot_any<TL>(Al, p, q, partial, st);                               // q = A p, (p, q)
-    finalize(partial, nb, scal, F_ALPHA, nullptr, 0, st);                  // alpha
-    cg_update_kernel<TL><<<nb, KT, 0, st>>>(d, r, p, q, scal, partial, n);  // d, r, (r, r)
-    finalize(partial, nb, scal, F_BETA, nullptr, 0, st);                   // beta
-    cg_dir_kernel<TL><<<nb, KT, 0, st>>>(p, r, scal, n);                   // p
+    launch_dot(dot_lo, Al, p, q, nullptr, fin(F_ALPHA, 0), st);                  // q = A p, (p, q), alpha
+    cg_update_kernel<TL><<<g_upd, KT, 0, st>>>(d, r, p, q, fin(F_BETA, 0), n);  // d, r, (r, r), beta
+    cg_dir_kernel<TL><<<nb, KT, 0, st>>>(p, r, scal, n);                        // p
   };
 
   cudaGraphExec_t exec = nullptr;
@@ -433,8 +503,7 @@ static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, doubl
   double rel = 0.0;
   rc = PJDS_OK;
   for (int outer = 0;; ++outer) {
-    launch_spmv_dot<double, double, 1>(Ah, x, r64, b, partial, s);  // r64 = b - A x
-    finalize(partial, nb, scal, F_NORM, nullptr, 0, s);
+    launch_dot(dot_res, Ah, x, r64, b, fin(F_NORM, 0), s);  // r64 = b - A x, ||r64||
     if ((rc = launch_check("cg residual"))) break;
     double rn = 0.0;
     e = cudaMemcpyAsync(&rn, scal + S_NRM, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -446,8 +515,7 @@ static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, doubl
     rel = bnorm > 0.0 ? rn / bnorm : rn;
     if (out.n_history < PJDS_CG_HISTORY) out.history[out.n_history++] = rel;
     if (outer >= o.max_outer || rel <= o.tol || rn == 0.0) break;
-    ir_start_kernel<TL><<<nb, KT, 0, s>>>(r64, r, p, d, scal, partial, n);
-    finalize(partial, nb, scal, F_RR, nullptr, 0, s);
+    ir_start_kernel<TL><<<g_start, KT, 0, s>>>(r64, r, p, d, fin(F_RR, 0), n);
     if (exec) {
       e = cudaGraphLaunch(exec, s);
       if (e != cudaSuccess) {
@@ -525,17 +593,22 @@ static int lanczos_run(const pjds_dev *A, const TX *v0, int32_t steps, double *a
   double *beta = cv.take<double>((size_t)steps + 1);
   TX *v = cv.take<TX>((size_t)n), *vp = cv.take<TX>((size_t)n), *w = cv.take<TX>((size_t)n);
   cudaError_t e = cudaMemsetAsync(beta, 0, sizeof(double) * ((size_t)steps + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, S_COUNT * sizeof(double), s);
   if (e != cudaSuccess) return set_error(PJDS_ECUDA, "lanczos: %s", cudaGetErrorString(e));
-  sumsq_kernel<TX><<<nb, KT, 0, s>>>(v0, partial, n);
-  finalize(partial, nb, scal, F_NORM, nullptr, 0, s);
+  Dot<TX, 0> dot;
+  int32_t g_sumsq = 0, g_orth = 0;
+  int rc;
+  if ((rc = make_dot(A, &dot)) || (rc = red_grid(sumsq_kernel<TX>, n, &g_sumsq)) ||
+      (rc = red_grid(lanczos_orth_kernel<TX>, n, &g_orth)))
+    return rc;
+  sumsq_kernel<TX><<<g_sumsq, KT, 0, s>>>(v0, Fin{partial, scal, nullptr, F_NORM, 0}, n);
   lanczos_start_kernel<TX><<<nb, KT, 0, s>>>(v0, v, vp, scal, n);
-  int rc = launch_check("lanczos start");
+  rc = launch_check("lanczos start");
   if (rc) return rc;
   auto step = [&](int32_t j, cudaStream_t st) {
-    spmv_dot_any<TX>(A, v, w, partial, st);  // w = A v, (v, w)
-    finalize(partial, nb, scal, F_LALPHA, alpha, j, st);
-    lanczos_orth_kernel<TX><<<nb, KT, 0, st>>>(w, v, vp, alpha, beta, j, partial, n);
-    finalize(partial, nb, scal, F_LBETA, beta, j + 1, st);
+    launch_dot(dot, A, v, w, nullptr, Fin{partial, scal, alpha, F_LALPHA, j}, st);  // w = A v, alpha_j = (v, w)
+    lanczos_orth_kernel<TX>
+        <<<g_orth, KT, 0, st>>>(w, v, vp, alpha, beta, j, Fin{partial, scal, beta, F_LBETA, j + 1}, n);  // beta_j+1
     lanczos_next_kernel<TX><<<nb, KT, 0, st>>>(vp, v, w, scal, basis ? basis + (int64_t)j * n : nullptr, n);
   };
   if (use_graph) {
@@ -723,16 +796,22 @@ extern "C" int pjds_ritz_refine(const pjds_dev *A_hi, const void *basis, int32_t
   double *sd = cv.take<double>((size_t)k);
   double *w = cv.take<double>((size_t)n);
   cudaError_t e = cudaMemcpyAsync(sd, s_host, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, S_COUNT * sizeof(double), st);
   if (e != cudaSuccess) return set_error(PJDS_ECUDA, "ritz: %s", cudaGetErrorString(e));
+  const Fin f_yy{partial, scal, nullptr, F_STORE, S_AUX0}, f_yw{partial, scal, nullptr, F_STORE, S_AUX1},
+      f_ee{partial, scal, nullptr, F_STORE, S_AUX2};
+  Dot<double, 0> dot;
+  int32_t g_comb = 0, g_res = 0;
+  if ((rc = make_dot(A_hi, &dot)) || (rc = red_grid(ritz_residual_kernel, n, &g_res)) ||
+      (rc = basis_dtype == PJDS_F64 ? red_grid(ritz_combine_kernel<double>, n, &g_comb)
+                                    : red_grid(ritz_combine_kernel<float>, n, &g_comb)))
+    return rc;
   if (basis_dtype == PJDS_F64)
-    ritz_combine_kernel<double><<<nb, KT, 0, st>>>(static_cast<const double *>(basis), sd, k, n, y, partial);
+    ritz_combine_kernel<double><<<g_comb, KT, 0, st>>>(static_cast<const double *>(basis), sd, k, n, y, f_yy);
   else
-    ritz_combine_kernel<float><<<nb, KT, 0, st>>>(static_cast<const float *>(basis), sd, k, n, y, partial);
-  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX0, st);              // (y, y)
-  launch_spmv_dot<double, double, 0>(A_hi, y, w, nullptr, partial, st);  // w = A y, (y, w)
-  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX1, st);
-  ritz_residual_kernel<<<nb, KT, 0, st>>>(w, y, scal, partial, n);
-  finalize(partial, nb, scal, F_STORE, nullptr, S_AUX2, st);
+    ritz_combine_kernel<float><<<g_comb, KT, 0, st>>>(static_cast<const float *>(basis), sd, k, n, y, f_yy);
+  launch_dot(dot, A_hi, y, w, nullptr, f_yw, st);  // w = A y, (y, w)
+  ritz_residual_kernel<<<g_res, KT, 0, st>>>(w, y, f_ee, n);
   if ((rc = launch_check("ritz refine"))) return rc;
   double h[3];
   e = cudaMemcpyAsync(h, scal + S_AUX0, sizeof(h), cudaMemcpyDeviceToHost, st);
