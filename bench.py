@@ -278,6 +278,7 @@ def run_ours(args, world, rank, local_rank):
         side = side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes)
         prec_gpu = precision_gpu_leg(torch, pjds, args, dev, flush)
         side["side"]["batching"] = batching_leg(torch, pjds, args, dev, flush)
+        side["side"]["small_case"] = small_case_leg(torch, pjds, args, dev, flush)
 
     # ---------------- end to end through the C ABI from pinned host memory
     xh = torch.from_numpy(x).pin_memory()
@@ -415,6 +416,59 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return {"side": out}
+
+
+def small_case_leg(torch, pjds, args, dev, flush):
+    """The banded N = 20,000 case (~451k nonzeros, 5.8 MB: L2-resident and
+    launch bound): per-launch time with L2 warm and flushed, and 1000
+    products captured in one CUDA graph, for pJDS and ELLPACK-R."""
+    med = statistics.median
+    import synth
+    A = synth.banded_uniform(n=20_000, seed=args.seed)
+    x = torch.from_numpy(synth.vector(A.n_cols, seed=args.seed)).to(dev)
+    nbytes = alg_bytes(A.n_rows, A.n_cols, A.nnz, 8, 8)
+    ell_bytes = alg_bytes(A.n_rows, A.n_cols, A.nnz, 8, 8, scatter=False) + 4 * A.n_rows
+    out = {"matrix": f"banded N={A.n_rows} nnz={A.nnz}", "alg_bytes": nbytes}
+    for fmt in ("pjds", "ellr"):
+        H = (pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64") if fmt == "pjds"
+             else pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype="f64"))
+        D = H.to_device(dev)
+        H.destroy()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+        run = (lambda: pjds.pjds_spmv(D, x, y)) if fmt == "pjds" else (lambda: pjds.ellr_spmv(D, x, y))
+        nb = nbytes if fmt == "pjds" else ell_bytes
+        hot = med(time_launches(torch, run, 200, 10, None))
+        cold = med(time_launches(torch, run, 50, 3, flush))
+        y_ref = y.clone()
+        side_stream = torch.cuda.Stream(device=dev)
+        side_stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side_stream):
+            run()
+        torch.cuda.current_stream().wait_stream(side_stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(1000):
+                run()
+        y.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        same = bool(torch.equal(y, y_ref))
+        reps = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            reps.append(e0.elapsed_time(e1) * 1e-3 / 1000)
+        t_g = med(reps)
+        out[fmt] = {"hot_us": round(hot * 1e6, 2), "hot_gbs": round(nb / hot / 1e9, 1),
+                    "cold_us": round(cold * 1e6, 2), "cold_gbs": round(nb / cold / 1e9, 1),
+                    "graph1000_us_per_product": round(t_g * 1e6, 3), "graph1000_gbs": round(nb / t_g / 1e9, 1),
+                    "graph_result_bit_identical": same}
+        del g, D, y
+    torch.cuda.synchronize()
+    return out
 
 
 def precision_gpu_leg(torch, pjds, args, dev, flush):

@@ -124,13 +124,20 @@ int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const in
 int pjds_destroy(pjds_host *h);
 
 /*
- * y = A x with A in pJDS (Listing 2): one thread per sorted row i computes
- * sum_{j < len(i)} val[col_start[j] + i] * x[col[col_start[j] + i]] in the
- * row's original entry order with fused multiply-add, then
+ * y = A x with A in pJDS (Listing 2): each sorted row i computes
+ * sum_{j < len(i)} val[col_start[j] + i] * x[col[col_start[j] + i]] with
+ * fused multiply-add, then
  *   - permute_cols = 0: writes y[perm[i]] (x and y in the original basis);
  *   - permute_cols = 1: writes y[i] (x and y in the permuted basis).
  * x: n_cols elements, y: n_rows elements, device memory of the vector type of
  * A->dtype; x and y must not overlap. Every element of y is written.
+ * Mapping (the default of pjds_spmv_cfg): one thread per row, summing in the
+ * row's original entry order, when n_rows >= 2^19 (fp64) or 2^20 (fp32, bf16)
+ * and every row is shorter than 64; otherwise T = 2, 4 or 8 threads share a
+ * row (each sums every T-th entry in order, then a fixed shuffle tree adds
+ * the T partial sums), T being the smallest with n_rows * T reaching that
+ * thread count, and at least 2 for rows of 64 entries or more.
+ * pjds_spmv_resolve reports the mapping chosen for a matrix.
  */
 int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
 

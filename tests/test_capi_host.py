@@ -188,14 +188,40 @@ def test_gpu_test_configs_resolve_on_host(P):
         assert P.pjds_spmv_resolve(H)["unroll"] in (4, 8)
 
 
+def _band(n, length, long_row=-1):
+    # n x n, row i holds columns i, i+1, ... (mod n); row long_row holds 64
+    lens = np.full(n, length, np.int64)
+    if long_row >= 0:
+        lens[long_row] = 64
+    row_ptr = np.zeros(n + 1, np.int64)
+    row_ptr[1:] = np.cumsum(lens)
+    rows = np.repeat(np.arange(n), lens)
+    col = ((rows + np.arange(row_ptr[-1]) - row_ptr[rows]) % n).astype(np.int32)
+    return synth.Crs(n, n, row_ptr, col, np.ones(row_ptr[-1]))
+
+
 def test_resolve_defaults(P):
     A = synth.hmep_like(n=10_000, seed=1)
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
-    assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128, "unroll": 4,
+    # 10k rows: one thread per row would leave the GPU short of threads
+    assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 8, "block_threads": 128, "unroll": 4,
                                       "staged": 0, "index64": 0}
+    # fill rule: smallest T in 1, 2, 4, 8 with n_rows * T >= 2^19 (fp64) / 2^20 (fp32, bf16)
+    for n, t64, t32 in ((600_000, 1, 2), (300_000, 2, 4), (100_000, 8, 8), (70_000, 8, 8), (1_100_000, 1, 1),
+                        (262_144, 2, 4), (262_143, 4, 8)):
+        C = _band(n, 3)
+        for dt, t in (("f64", t64), ("f32", t32), ("bf16", t32)):
+            HC = P.pjds_create(C.n_rows, C.n_cols, C.row_ptr, C.col, C.val, b=32, dtype=dt)
+            r = P.pjds_spmv_resolve(HC)
+            assert r["threads_per_row"] == t and r["rows_per_thread"] == 1, (n, dt, r)
+            HC.destroy()
     Z = synth.zipf_rows(10_000, s=2.0, len_max=512, seed=1)
     HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
-    assert P.pjds_spmv_resolve(HZ)["threads_per_row"] == 2
+    assert P.pjds_spmv_resolve(HZ)["threads_per_row"] == 8
+    # enough rows for one thread per row, but one row of 64 entries: 2 threads per row
+    L = _band(600_000, 3, long_row=12345)
+    HL = P.pjds_create(L.n_rows, L.n_cols, L.row_ptr, L.col, L.val, b=32)
+    assert P.pjds_spmv_resolve(HL)["threads_per_row"] == 2
     assert P.pjds_spmv_resolve(HZ, rows_per_thread=2)["threads_per_row"] == 1
     with pytest.raises(P.PjdsError):
         P.pjds_spmv_resolve(HZ, unroll=16)

@@ -154,10 +154,11 @@ def test_staged_kernel_bitwise_and_status(P, dtype, b):
 
 
 def test_row_sums_exact(P, oracle_lib):
-    # x = 1: each fused multiply-add adds val exactly like the oracle's sum.
+    # x = 1: with one thread per row each fused multiply-add adds val exactly
+    # like the oracle's sum, in the same order.
     A = synth.hmep_like(n=200_000, seed=21)
     x = np.ones(A.n_cols)
-    y, _, _ = run_pjds(P, A, x)
+    y, _, _ = run_pjds(P, A, x, cfg=dict(threads_per_row=1))
     assert np.array_equal(y, oracle_lib.crs_spmv(A, x))
 
 
