@@ -46,10 +46,10 @@ L2_FLUSH_BYTES = 256 << 20
 # while the kernel's source (spmv_kernels.cuh) hashes to the recorded value and
 # the launch configuration is the recorded one.
 NCU_TRAFFIC = {
-    # profiles/pjds_rows_kernel_hmep6.2M_f64.md: 1.62 GB read + 161 MB write per launch
-    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_781_000_000, "src": "81997970780652d8",
+    # profiles/pjds_rows_kernel_hmep6.2M_f64.md: 1.192 GB read + 22.9 MB write per launch
+    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_215_038_976, "src": "c40c4fc59d3c4bbb",
                                    "cfg": {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 128,
-                                           "unroll": 4, "staged": 0, "index64": 0}},
+                                           "unroll": 4, "staged": 0, "index64": 0, "tile_order": 1}},
 }
 
 
@@ -337,7 +337,8 @@ def run_ours(args, world, rank, local_rank):
         "gflops": round(value * 2 * A.nnz / nbytes, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "pjds_rows_kernel<double,double,int,R=1,U=4,scatter> 128 thr/CTA", "peak_kind": peak_kind},
+                     "kernel": "pjds_rows_kernel<double,double,int,R=1,U=4,scatter> 128 thr/CTA, tile order",
+                     "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": 8 * A.n_cols,
                 "d2h_bytes_per_step": 8 * A.n_rows},
@@ -409,7 +410,7 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
     del Dp, xp, yp
 
     for cfg in ({"rows_per_thread": 2}, {"rows_per_thread": 4}, {"threads_per_row": 2}, {"block_threads": 512},
-                {"block_threads": 128}, {"staged": 1}):
+                {"block_threads": 128}, {"staged": 1}, {"tile_order": -1}):
         tc = med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xt, y, **cfg), K, W, flush))
         key = "cfg_" + "_".join(f"{k}{v}" for k, v in cfg.items())
         out[key] = {"gbs": round(nbytes / tc / 1e9, 1), "us": round(tc * 1e6, 2)}
@@ -497,7 +498,7 @@ def precision_gpu_leg(torch, pjds, args, dev, flush):
         vb = {"f64": 8, "f32": 4, "bf16": 2}[dt]
         xb = 8 if dt == "f64" else 4
         nb = alg_bytes(n, n, S.nnz, vb, xb, scatter=False)
-        for tag, kw in (("", {}), ("_staged", {"staged": 1})):
+        for tag, kw in (("", {}), ("_staged", {"staged": 1}), ("_sorted_order", {"tile_order": -1})):
             t = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xv, yv, **kw), 10, 3, flush))
             rep[f"spmv_{dt}{tag}"] = {"gbs": round(nb / t / 1e9, 1), "us": round(t * 1e6, 2),
                                       "frac_of_hbm": round(nb / t / 1e9 / hbm_peak()[0], 4)}
@@ -548,6 +549,19 @@ def precision_gpu_leg(torch, pjds, args, dev, flush):
     if "f64" in lan and "f32" in lan:
         rep["theta_refined_f32_vs_f64_rel"] = abs(lan["f32"]["theta_refined_fp64"] -
                                                   lan["f64"]["theta_refined_fp64"]) / abs(lan["f64"]["theta_refined_fp64"])
+    # the fp64 CG once more with the tiles in sorted order (no traversal table)
+    Hn = pjds.pjds_create(S.n_rows, S.n_cols, S.row_ptr, S.col, S.val, b=32, dtype="f64", permute_cols=True)
+    Dn = Hn.to_device(dev, tile_order=False)
+    Hn.destroy()
+    xp = torch.zeros_like(bp)
+    krylov.cg_solve(Dn, None, bp, xp, max_outer=1, inner_iters=300)
+    xp.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    krylov.cg_solve(Dn, None, bp, xp, max_outer=1, inner_iters=300)
+    torch.cuda.synchronize()
+    rep["cg_fp64_sorted_order_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+    del Dn, xp
     f64 = rep["cg_fp64"]["ms"]
     for name in ("cg_f32_refined", "cg_bf16_refined"):
         rep[name]["speedup_vs_fp64"] = round(f64 / rep[name]["ms"], 3)

@@ -75,6 +75,16 @@ void pjds_abi_sizes(int32_t out[5]);
  * iterative solver runs entirely on permuted vectors (Sect. 2.1).
  * val holds n_stored elements of dtype (double, float, or bfloat16 as uint16
  * bits, rounded to nearest even from the fp64 input).
+ * tile_order is not part of the storage format: it is the order in which the
+ * product kernels take the 32-row tiles of the sorted matrix (tile t = sorted
+ * rows 32t .. 32t+31; n_pad / 32 tiles). Sect. 2.1 fixes which rows share a
+ * block, not the order in which blocks are processed; pjds_create lists the
+ * tiles by the original index of their first row (ascending, stable; tiles
+ * holding only padding rows last), so that the rows in flight at any moment
+ * lie close together in the original numbering, whatever their length. Their
+ * x gathers then share L2 sectors and their scattered y stores fill whole
+ * sectors while the lines are still in L2. Each row's arithmetic does not
+ * depend on the order.
  */
 typedef struct pjds_host {
   int32_t n_rows, n_cols, n_pad, b, n_blocks, n_max;
@@ -87,12 +97,19 @@ typedef struct pjds_host {
   int64_t *col_start; /* [n_max+1]  */
   int32_t *col;       /* [n_stored] */
   void *val;          /* [n_stored] of dtype */
+  int32_t *tile_order; /* [n_pad / 32] */
 } pjds_host;
 
 /*
  * Device-side view of the same arrays: the caller copies each host array into
  * a device buffer it owns and fills this struct (sizes copied from the host
  * struct). row_len and inv_perm are not read by the kernels and may be NULL.
+ * tile_order may be NULL (tiles in sorted order); otherwise it must hold the
+ * n_pad / 32 entries pjds_create wrote (a permutation of 0 .. n_pad/32 - 1).
+ * The one-thread-per-row, several-rows-per-thread and several-threads-per-row
+ * kernels follow it when pjds_launch.tile_order selects it (a kernel skips an
+ * entry outside that range); the staged kernel, SpMM, the batched launch and
+ * the Krylov products take tiles in sorted order.
  * val must be 16-byte aligned; all other pointers 4-byte aligned.
  */
 typedef struct pjds_dev {
@@ -105,6 +122,7 @@ typedef struct pjds_dev {
   const int64_t *col_start;
   const int32_t *col;
   const void *val;
+  const int32_t *tile_order; /* NULL: tiles in sorted order */
 } pjds_dev;
 
 /*
@@ -163,6 +181,15 @@ int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
  *                    Its waits are bounded; a wait that runs out sets a bit
  *                    in the device status word (pjds_device_status) and the
  *                    affected rows of y are not written.
+ *   tile_order       0: automatic, 1: take the 32-row tiles in A->tile_order
+ *                    (PJDS_EINVAL if A->tile_order is NULL), -1: in sorted
+ *                    order. Automatic uses the table when there is one,
+ *                    n_rows >= 2^20 and the longest row has at most 4 times
+ *                    the mean row length (a measured GB300 rule: ordering
+ *                    gains 4-23% there, while on smaller matrices nothing is
+ *                    gained and on widely spread row lengths the sorted
+ *                    order's longest-first schedule is worth more, 5-25%).
+ *                    The staged kernel always takes sorted order.
  * rows_per_thread > 1 and threads_per_row > 1 are exclusive. Invalid values
  * return PJDS_EINVAL.
  */
@@ -174,7 +201,8 @@ typedef struct pjds_launch {
   int32_t staged;
   int32_t index64;  /* 1: 64-bit element offsets even when 32 bits suffice (they are
                        used automatically from 2^31 stored entries on) */
-  int32_t reserved[2];
+  int32_t tile_order;
+  int32_t reserved;
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);

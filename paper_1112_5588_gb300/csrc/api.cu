@@ -42,6 +42,7 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   if (T != 1 && T != 2 && T != 4 && T != 8) return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
   if (R > 1 && T > 1) return set_error(PJDS_EINVAL, "rows_per_thread > 1 needs threads_per_row = 1");
   if (c.staged) {
+    c.tile_order = 0;
     if (R != 1 || T != 1) return set_error(PJDS_EINVAL, "the staged kernel runs one thread per row");
     if (((uintptr_t)A->val | (uintptr_t)A->col) & 15)
       return set_error(PJDS_EINVAL, "the staged kernel needs 16-byte aligned val and col");
@@ -62,11 +63,6 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   return PJDS_OK;
 }
 
-// Default configuration, from sweeps on GB300 (HMEp-like, stencil, Zipf and
-// DLR-like matrices): one thread per row (the paper's mapping) with 4 (fp64,
-// bf16) or 8 (fp32) jagged diagonals per load round; matrices whose longest
-// row has 64 or more entries use two threads per row. pjds_spmv_cfg
-// overrides any field.
 // Default mapping: one row per thread, and T threads per row where one
 // thread per row leaves the GPU short of threads or rows are long. T is the
 // smallest of 1, 2, 4, 8 with n_rows * T >= 2^19 threads (fp64) or 2^20
@@ -87,6 +83,7 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   c.unroll = 0;  // filled in by check_cfg once R and T are final
   c.staged = 0;
   c.index64 = 0;
+  c.tile_order = auto_tile_order(A) ? 1 : 0;
   return c;
 }
 
@@ -116,6 +113,9 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
     if (cfg->unroll) c.unroll = cfg->unroll;
     if (cfg->index64) c.index64 = 1;
+    if (cfg->tile_order < -1 || cfg->tile_order > 1) return set_error(PJDS_EINVAL, "tile_order must be -1, 0 or 1");
+    if (cfg->tile_order == 1 && !A->tile_order) return set_error(PJDS_EINVAL, "tile_order = 1 but A->tile_order is NULL");
+    if (cfg->tile_order) c.tile_order = cfg->tile_order == 1;
     if (cfg->staged) {
       c.staged = 1;
       if (!cfg->rows_per_thread) c.rows_per_thread = 1;
@@ -139,7 +139,8 @@ extern "C" int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds
   out->unroll = c.unroll;
   out->staged = c.staged;
   out->index64 = c.index64;
-  out->reserved[0] = out->reserved[1] = 0;
+  out->tile_order = c.tile_order ? 1 : -1;
+  out->reserved = 0;
   return PJDS_OK;
 }
 

@@ -361,7 +361,17 @@ extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const voi
       t0 += rows;
     }
   }
-  std::stable_sort(tiles.begin(), tiles.end(), [](const T &a, const T &b) { return a.cost > b.cost; });
+  // matrices by total work per lane (largest first), tiles by work per lane
+  // inside each matrix: the CTAs share one or two matrices' x at a time
+  std::vector<int64_t> mcost((size_t)n_mats, 0);
+  for (const T &t : tiles) mcost[(size_t)t.m] += t.cost;
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const T &a, const T &b) {
+    if (a.m != b.m) {
+      const int64_t ca = mcost[(size_t)a.m], cb = mcost[(size_t)b.m];
+      return ca != cb ? ca > cb : a.m < b.m;
+    }
+    return a.cost > b.cost;
+  });
   std::vector<int4> tl(tiles.size());
   for (size_t i = 0; i < tiles.size(); ++i) tl[i] = make_int4(tiles[i].m, tiles[i].row0, tiles[i].rows, tiles[i].lanes);
   char *p = static_cast<char *>(plan_dev);

@@ -25,4 +25,12 @@ inline int value_bytes(int32_t dtype) {
 // Bytes of one vector element (x, y) for the given dtype.
 inline int vector_bytes(int32_t dtype) { return dtype == PJDS_F64 ? 8 : 4; }
 
+// Automatic choice of the tile traversal table (pjds_launch.tile_order = 0):
+// large matrices (n_rows >= 2^20) whose longest row is at most 4 times the
+// mean row length.
+inline bool auto_tile_order(const pjds_dev *A) {
+  if (!A->tile_order || A->n_rows < (1 << 20)) return false;
+  return (int64_t)A->n_max * A->n_rows <= 4 * A->nnz;
+}
+
 }  // namespace pjds

@@ -108,6 +108,7 @@ static void free_pjds(pjds_host *h) {
   free(h->col_start);
   free(h->col);
   free(h->val);
+  free(h->tile_order);
   free(h);
 }
 
@@ -130,7 +131,7 @@ using namespace pjds;
 
 extern "C" const char *pjds_last_error(void) { return g_msg; }
 
-extern "C" int32_t pjds_version(void) { return 2; }
+extern "C" int32_t pjds_version(void) { return 3; }
 
 extern "C" void pjds_abi_sizes(int32_t out[5]) {
   out[0] = (int32_t)sizeof(pjds_host);
@@ -235,6 +236,25 @@ extern "C" int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_pt
       col[o] = -1;
       clear_values(v, o, 1, dtype);
     }
+  }
+
+  // traversal order of the 32-row tiles: by the original index of each tile's
+  // first row (tiles of padding rows only at the end), stable
+  const int32_t n_tiles = n_pad / 32;
+  h->tile_order = alloc_n<int32_t>(n_tiles);
+  if (!h->tile_order) {
+    free_pjds(h);
+    return set_error(PJDS_ENOMEM, "out of host memory");
+  }
+  {
+    std::vector<int32_t> key((size_t)n_tiles);
+    for (int32_t t = 0; t < n_tiles; ++t) {
+      const int64_t first = (int64_t)t * 32;
+      key[(size_t)t] = first < n_rows ? perm[first] : std::numeric_limits<int32_t>::max();
+      h->tile_order[t] = t;
+    }
+    std::stable_sort(h->tile_order, h->tile_order + n_tiles,
+                     [&](int32_t a, int32_t c) { return key[(size_t)a] < key[(size_t)c]; });
   }
   *out = h;
   return PJDS_OK;

@@ -171,6 +171,8 @@ __global__ void __launch_bounds__(KT)
                     int32_t b) {
   const TV *__restrict__ val = static_cast<const TV *>(val_);
   double contrib = 0.0;
+  // rows in sorted order: the tile traversal table measured 1.7% slower here
+  // (fp64 CG on the 27-point stencil, 4.5M rows)
   for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n_rows; i += (int64_t)gridDim.x * KT) {
     const int32_t L = __ldg(block_len + (int32_t)(i / b));
     const auto acc = row_product<TV, TX, IDX>(val, col, col_start, L, i, x);

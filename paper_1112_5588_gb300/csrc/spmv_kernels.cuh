@@ -131,6 +131,16 @@ __device__ __forceinline__ bf16_t ld_stream1(const bf16_t *p) {
   return v;
 }
 
+// Tile traversal order: logical row r is row r mod 32 of tile order[r / 32]
+// (tiles of 32 sorted rows). Rewrites r in place; false for an entry outside
+// the table's range (the thread then has no row).
+__device__ __forceinline__ bool tile_row(const int32_t *__restrict__ order, int32_t n_pad, int64_t &r) {
+  const int32_t t = __ldg(order + (r >> 5));
+  if ((uint32_t)t >= (uint32_t)(n_pad >> 5)) return false;
+  r = (int64_t)t * 32 + (r & 31);
+  return true;
+}
+
 // Gather through the read-only L1 path; pads (c < 0) read nothing.
 template <typename TX>
 __device__ __forceinline__ TX gather(const TX *__restrict__ x, int32_t c) {
@@ -147,12 +157,14 @@ template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER>
 __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
                                                         const int64_t *__restrict__ col_start,
                                                         const int32_t *__restrict__ block_len,
-                                                        const int32_t *__restrict__ perm, const TX *__restrict__ x,
+                                                        const int32_t *__restrict__ perm,
+                                                        const int32_t *__restrict__ order, const TX *__restrict__ x,
                                                         TX *__restrict__ y, int32_t n_rows, int32_t n_pad, int32_t b) {
   using TA = typename Acc<TV>::T;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i0 = t * R;
+  int64_t i0 = t * R;
   if (i0 >= n_pad) return;
+  if (order && !tile_row(order, n_pad, i0)) return;
   const int32_t L = __ldg(block_len + (int32_t)(i0 / b));
   TA acc[R];
 #pragma unroll
@@ -206,13 +218,15 @@ template <typename TV, typename TX, typename IDX, int T, int U, bool SCATTER>
 __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
                                                         const int64_t *__restrict__ col_start,
                                                         const int32_t *__restrict__ block_len,
-                                                        const int32_t *__restrict__ perm, const TX *__restrict__ x,
+                                                        const int32_t *__restrict__ perm,
+                                                        const int32_t *__restrict__ order, const TX *__restrict__ x,
                                                         TX *__restrict__ y, int32_t n_rows, int32_t n_pad, int32_t b) {
   using TA = typename Acc<TV>::T;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = g / T;
+  int64_t i = g / T;
   const int32_t s = (int32_t)(g % T);
-  const bool active = i < n_pad;  // whole warps stay for the shuffles
+  bool active = i < n_pad;  // whole warps stay for the shuffles
+  if (active && order) active = tile_row(order, n_pad, i);
   const int32_t L = active ? __ldg(block_len + (int32_t)(i / b)) : 0;
   TA acc = TA(0);
   for (int32_t j = s; j < L; j += U * T) {
@@ -237,7 +251,7 @@ __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ va
   }
 #pragma unroll
   for (int off = T / 2; off >= 1; off /= 2) acc += __shfl_down_sync(0xffffffffu, acc, off, T);
-  if (s == 0 && i < n_rows) {
+  if (s == 0 && active && i < n_rows) {
     if constexpr (SCATTER)
       y[__ldcs(perm + i)] = (TX)acc;
     else

@@ -17,6 +17,7 @@ struct LaunchCfg {
   int unroll;           // U: jagged diagonals per chunk of the j-loop
   int staged;           // 1: bulk-copy staged persistent kernel (R = T = 1)
   int index64;          // 1: 64-bit element offsets regardless of size
+  int tile_order;       // 1: tiles taken in A->tile_order
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -54,7 +55,8 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
   if (grid <= 0) return PJDS_OK;
   if (grid > 0x7fffffffLL) return set_error(PJDS_EOVERFLOW, "grid too large");
   const dim3 g((unsigned)grid), blk((unsigned)nt);
-#define PJDS_ARGS val, A->col, A->col_start, A->block_len, A->perm, x, y, A->n_rows, A->n_pad, A->b
+  const int32_t *order = c.tile_order ? A->tile_order : nullptr;
+#define PJDS_ARGS val, A->col, A->col_start, A->block_len, A->perm, order, x, y, A->n_rows, A->n_pad, A->b
   const int U = c.unroll;
 #define PJDS_ROWS(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
 #define PJDS_TPR(TT, UU) dev::pjds_tpr_kernel<TV, TX, IDX, TT, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)

@@ -48,7 +48,8 @@ static Shape shape_for(int32_t n_rows, const int64_t *row_ptr, int32_t b) {
 
 static size_t matrix_bytes(const Shape &s, int32_t n_rows, int32_t dtype) {
   return a256((size_t)n_rows * 4) + a256((size_t)s.n_blocks * 4) + a256((size_t)(s.n_max + 1) * 8) +
-         a256((size_t)s.n_stored * 4) + a256((size_t)s.n_stored * value_bytes(dtype));
+         a256((size_t)s.n_stored * 4) + a256((size_t)s.n_stored * value_bytes(dtype)) +
+         a256((size_t)(s.n_pad / 32) * 4);
 }
 
 static size_t arena_need(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const pjds_candidate *c,
@@ -164,6 +165,7 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
     d.col_start = static_cast<const int64_t *>(place(h->col_start, (size_t)(h->n_max + 1) * 8));
     d.col = static_cast<const int32_t *>(place(h->col, (size_t)h->n_stored * 4));
     d.val = place(h->val, (size_t)h->n_stored * value_bytes(dt));
+    d.tile_order = static_cast<const int32_t *>(place(h->tile_order, (size_t)(h->n_pad / 32) * 4));
     void *x = p;
     p += a256((size_t)n_cols * 8);
     void *y = p;

@@ -41,19 +41,19 @@ class _PjdsHostS(ctypes.Structure):
     _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("inv_perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp),
-                ("col", _vp), ("val", _vp)]
+                ("col", _vp), ("val", _vp), ("tile_order", _vp)]
 
 
 class _PjdsDevS(ctypes.Structure):
     _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp), ("col", _vp),
-                ("val", _vp)]
+                ("val", _vp), ("tile_order", _vp)]
 
 
 class _LaunchS(ctypes.Structure):
     _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32),
-                ("staged", _i32), ("index64", _i32), ("reserved", _i32 * 2)]
+                ("staged", _i32), ("index64", _i32), ("tile_order", _i32), ("reserved", _i32)]
 
 
 class _EllrHostS(ctypes.Structure):
@@ -165,16 +165,19 @@ class PjdsHost:
         self.col_start = _np_view(s.col_start, s.n_max + 1, np.int64)
         self.col = _np_view(s.col, s.n_stored, np.int32)
         self.val = _np_view(s.val, s.n_stored, _VAL_NP[s.dtype])
+        self.tile_order = _np_view(s.tile_order, s.n_pad // 32, np.int32)
 
     def arrays(self) -> dict:
         """Copies of every array plus the sizes (survive destroy())."""
         out = {k: getattr(self, k) for k, _ in _PjdsHostS._fields_[:10]}
-        for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val"):
+        for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val", "tile_order"):
             out[k] = getattr(self, k).copy()
         return out
 
-    def to_device(self, device="cuda") -> "PjdsDevice":
-        return PjdsDevice(self, device)
+    def to_device(self, device="cuda", tile_order: bool = True) -> "PjdsDevice":
+        """Upload; tile_order=False leaves the traversal table out (tiles in
+        sorted order: same results, for comparisons)."""
+        return PjdsDevice(self, device, tile_order)
 
     def destroy(self):
         if self._ptr is not None:
@@ -203,7 +206,7 @@ def pjds_create(n_rows: int, n_cols: int, row_ptr, col, val, b: int = 32, dtype=
 class PjdsDevice:
     """Device copy of a pJDS matrix in torch-owned buffers plus its pjds_dev struct."""
 
-    def __init__(self, host: PjdsHost, device="cuda"):
+    def __init__(self, host: PjdsHost, device="cuda", tile_order: bool = True):
         dev = torch.device(device)
         self.device = dev
         self.dtype = host.dtype
@@ -221,6 +224,7 @@ class PjdsDevice:
         self.col_start = up(host.col_start, np.int64)
         self.col = up(host.col, np.int32)
         self.val = up(host.val, {0: np.float64, 1: np.float32, 2: np.int16}[host.dtype])
+        self.tile_order = up(host.tile_order, np.int32) if tile_order else None
         s = _PjdsDevS()
         for f, _ in _PjdsDevS._fields_[:10]:
             setattr(s, f, getattr(host, f))
@@ -230,6 +234,7 @@ class PjdsDevice:
         s.col_start = self.col_start.data_ptr() or None
         s.col = self.col.data_ptr() or None
         s.val = self.val.data_ptr() or None
+        s.tile_order = (self.tile_order.data_ptr() or None) if tile_order else None
         self._s = s
 
     @property
@@ -238,7 +243,7 @@ class PjdsDevice:
 
     def device_bytes(self) -> int:
         return sum(t.numel() * t.element_size() for t in (self.perm, self.block_len, self.row_len, self.col_start,
-                                                           self.col, self.val))
+                                                           self.col, self.val, self.tile_order) if t is not None)
 
 
 def _check_vec(t: torch.Tensor, n: int, dtype, name: str):
@@ -258,27 +263,28 @@ def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> t
 
 def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
                   threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, staged: int = 0,
-                  index64: int = 0, stream=None) -> torch.Tensor:
-    """y = A x with an explicit kernel configuration (pjds_spmv_cfg)."""
+                  index64: int = 0, tile_order: int = 0, stream=None) -> torch.Tensor:
+    """y = A x with an explicit kernel configuration (pjds_spmv_cfg).
+    tile_order: 0 automatic, 1 traversal table, -1 sorted order."""
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y
 
 
 def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, block_threads: int = 0,
-                      unroll: int = 0, staged: int = 0, index64: int = 0) -> dict:
+                      unroll: int = 0, staged: int = 0, index64: int = 0, tile_order: int = 0) -> dict:
     """The launch configuration pjds_spmv_cfg would use (no launch). `A` is a
     PjdsDevice or a PjdsHost (only sizes and alignment are read)."""
     s = A.struct if isinstance(A, PjdsDevice) else _dev_struct_from_host(A)
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order)
     out = _LaunchS()
     _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
             "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged,
-            "index64": out.index64}
+            "index64": out.index64, "tile_order": out.tile_order}
 
 
 def pjds_wait_selftest(which: int = 0, stream=None) -> None:
@@ -299,6 +305,7 @@ def _dev_struct_from_host(H: "PjdsHost"):
         setattr(s, f, getattr(H, f))
     # alignment of torch allocations (512 B) stands in for the device pointers
     s.val = s.col = s.col_start = s.block_len = s.perm = 512
+    s.tile_order = 512 if len(H.tile_order) else None
     return s
 
 

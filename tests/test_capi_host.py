@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(P):
 
 
 def test_abi_version_and_struct_sizes(P):
-    assert P.lib().pjds_version() == 2  # the binding itself checked the struct sizes on load
+    assert P.lib().pjds_version() == 3  # the binding itself checked the struct sizes on load
 
 
 CASES = [
@@ -205,7 +205,7 @@ def test_resolve_defaults(P):
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
     # 10k rows: one thread per row would leave the GPU short of threads
     assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 8, "block_threads": 128, "unroll": 4,
-                                      "staged": 0, "index64": 0}
+                                      "staged": 0, "index64": 0, "tile_order": -1}
     # fill rule: smallest T in 1, 2, 4, 8 with n_rows * T >= 2^19 (fp64) / 2^20 (fp32, bf16)
     for n, t64, t32 in ((600_000, 1, 2), (300_000, 2, 4), (100_000, 8, 8), (70_000, 8, 8), (1_100_000, 1, 1),
                         (262_144, 2, 4), (262_143, 4, 8)):
@@ -218,13 +218,37 @@ def test_resolve_defaults(P):
     Z = synth.zipf_rows(10_000, s=2.0, len_max=512, seed=1)
     HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
     assert P.pjds_spmv_resolve(HZ)["threads_per_row"] == 8
+    assert P.pjds_spmv_resolve(HZ, rows_per_thread=2)["threads_per_row"] == 1
+    with pytest.raises(P.PjdsError):
+        P.pjds_spmv_resolve(HZ, unroll=16)
     # enough rows for one thread per row, but one row of 64 entries: 2 threads per row
     L = _band(600_000, 3, long_row=12345)
     HL = P.pjds_create(L.n_rows, L.n_cols, L.row_ptr, L.col, L.val, b=32)
     assert P.pjds_spmv_resolve(HL)["threads_per_row"] == 2
-    assert P.pjds_spmv_resolve(HZ, rows_per_thread=2)["threads_per_row"] == 1
-    with pytest.raises(P.PjdsError):
-        P.pjds_spmv_resolve(HZ, unroll=16)
+
+
+def test_resolve_tile_order_rule(P):
+    # automatic: the traversal table from 2^20 rows on when the longest row is
+    # at most 4 times the mean row length; 1 / -1 force it on / off
+    big = P.pjds_create(*(lambda C: (C.n_rows, C.n_cols, C.row_ptr, C.col, C.val))(_band(1 << 20, 3)), b=32)
+    assert P.pjds_spmv_resolve(big)["tile_order"] == 1
+    assert P.pjds_spmv_resolve(big, threads_per_row=4)["tile_order"] == 1
+    assert P.pjds_spmv_resolve(big, tile_order=-1)["tile_order"] == -1
+    assert P.pjds_spmv_resolve(big, staged=1)["tile_order"] == -1
+    small = P.pjds_create(*(lambda C: (C.n_rows, C.n_cols, C.row_ptr, C.col, C.val))(_band((1 << 20) - 1, 3)), b=32)
+    assert P.pjds_spmv_resolve(small)["tile_order"] == -1
+    assert P.pjds_spmv_resolve(small, tile_order=1)["tile_order"] == 1
+    spread = P.pjds_create(*(lambda C: (C.n_rows, C.n_cols, C.row_ptr, C.col, C.val))(
+        _band(1 << 20, 3, long_row=5)), b=32)  # longest 64 > 4 x mean (~3)
+    assert P.pjds_spmv_resolve(spread)["tile_order"] == -1
+    for bad in (2, -2):
+        with pytest.raises(P.PjdsError):
+            P.pjds_spmv_resolve(big, tile_order=bad)
+    s = P._dev_struct_from_host(big)
+    s.tile_order = None  # no table: forcing it is an error, automatic falls back
+    cfg, out = P._LaunchS(0, 0, 0, 0, 0, 0, 1), P._LaunchS()
+    assert P.lib().pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)) == -1
+    assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(out)) == 0 and out.tile_order == -1
 
 
 def test_staged_option_resolves(P):
@@ -239,3 +263,24 @@ def test_staged_option_resolves(P):
     cfg = P._LaunchS(0, 0, 0, 0, 1)
     out = P._LaunchS()
     assert P.lib().pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)) == -1
+
+
+@pytest.mark.parametrize("b", [32, 64, 256])
+def test_tile_order_definition(P, b):
+    # the traversal table lists the 32-row tiles of the sorted matrix by the
+    # original index of their first row (stable), tiles of padding rows last
+    for A in (synth.hmep_like(n=20_000, seed=3), tiny.random_lengths(1037, 900, max_len=70, seed=5, p_empty=0.2),
+              synth.zipf_rows(5_000, s=2.0, len_max=300, seed=2), tiny.from_lengths([0] * 40, 7)):
+        H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b)
+        n_t = H.n_pad // 32
+        first = np.arange(n_t) * 32
+        key = np.full(n_t, np.iinfo(np.int64).max)
+        real = first < A.n_rows
+        key[real] = H.perm[first[real]]
+        want = np.argsort(key, kind="stable")
+        assert np.array_equal(H.tile_order, want)
+        assert np.array_equal(np.sort(H.tile_order), np.arange(n_t))
+        # keys of consecutive tiles never decrease
+        k = key[H.tile_order]
+        assert np.all(k[1:] >= k[:-1])
+        H.destroy()

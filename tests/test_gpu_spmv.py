@@ -255,3 +255,55 @@ def test_stream_argument_is_used(P):
         P.pjds_spmv(D, xt, y, stream=s)
     s.synchronize()
     assert np.array_equal(y.cpu().numpy(), y_ref)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("b,permute", [(32, False), (64, True), (256, False)])
+def test_tile_order_bitwise_equal_to_sorted_order(P, dtype, b, permute):
+    # the traversal table only changes which warp takes which 32-row tile:
+    # every kernel that follows it writes the same bits as without it
+    torch = _torch()
+    for A in (synth.hmep_like(n=150_000, seed=41), synth.zipf_rows(30_000, s=1.8, len_max=400, seed=42),
+              tiny.random_lengths(1037, 1037, max_len=70, seed=43, p_empty=0.15)):
+        H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b, dtype=dtype, permute_cols=permute)
+        Do, Dn = H.to_device("cuda"), H.to_device("cuda", tile_order=False)
+        assert Do.struct.tile_order and not Dn.struct.tile_order
+        x = torch.from_numpy(synth.vector(A.n_cols, seed=44)).to("cuda", Do.vec_dtype)
+        for cfg in (dict(threads_per_row=1), dict(rows_per_thread=2), dict(rows_per_thread=4), dict(threads_per_row=2),
+                    dict(threads_per_row=8, block_threads=64), dict(), dict(index64=1), dict(rows_per_thread=2, index64=1)):
+            yo = torch.full((A.n_rows,), float("nan"), dtype=Do.vec_dtype, device="cuda")
+            yn = torch.full_like(yo, float("nan"))
+            P.pjds_spmv_cfg(Do, x, yo, tile_order=1, **cfg)
+            P.pjds_spmv_cfg(Dn, x, yn, **cfg)
+            torch.cuda.synchronize()
+            assert torch.equal(yo.view(torch.int16 if dtype != "f64" else torch.int64),
+                               yn.view(torch.int16 if dtype != "f64" else torch.int64)), (cfg, A.n_rows)
+        H.destroy()
+
+
+def test_tile_order_entry_out_of_range_is_skipped(P):
+    # an entry outside 0 .. n_pad/32 - 1 is skipped by the kernels' range check:
+    # the rows of the tile it replaced are not written, every other row is
+    torch = _torch()
+    A = synth.hmep_like(n=20_000, seed=45)
+    x = synth.vector(A.n_cols, seed=45)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, permute_cols=True)
+    D = H.to_device("cuda")
+    n_t = H.n_pad // 32
+    bad = D.tile_order.clone()
+    lost = int(bad[7].item())
+    bad[7] = n_t
+    D.tile_order = bad
+    D.struct.tile_order = bad.data_ptr()
+    xt = torch.from_numpy(x[H.perm]).cuda()
+    Dn = H.to_device("cuda", tile_order=False)
+    skipped = torch.zeros(A.n_rows, dtype=torch.bool, device="cuda")
+    skipped[lost * 32:min(lost * 32 + 32, A.n_rows)] = True
+    for cfg in (dict(threads_per_row=1), dict(threads_per_row=4), dict(rows_per_thread=2)):
+        y = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+        ref = torch.empty_like(y)
+        P.pjds_spmv_cfg(D, xt, y, tile_order=1, **cfg)
+        P.pjds_spmv_cfg(Dn, xt, ref, **cfg)
+        torch.cuda.synchronize()
+        assert torch.isnan(y[skipped]).all(), cfg
+        assert torch.equal(y[~skipped], ref[~skipped]), cfg
