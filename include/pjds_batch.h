@@ -26,8 +26,10 @@ extern "C" {
  * (element (r, c) at r*k + c), device memory of A's vector type (double for
  * PJDS_F64, float otherwise), 16-byte aligned. k: 1, or a multiple of 4 up to
  * 128 (float) / a multiple of 2 up to 64 (double). Each thread handles one
- * row and 16 bytes of its k columns, so the lanes of a row read each
- * gathered row of X as one contiguous segment. Column c of Y is computed in
+ * row and 16 or 32 bytes of its k columns (32 when that leaves at least two
+ * threads per row, the rows are not widely spread in length and the launch
+ * still has 2^19 threads), so the lanes of a row read each gathered row of X
+ * as one contiguous segment. Column c of Y is computed in
  * the same order and with the same fused multiply-adds as pjds_spmv with one
  * thread per row on column c of X. Original basis (permute_cols = 0): row i of
  * the sorted matrix is written to row perm[i] of Y; permuted basis: to row i.

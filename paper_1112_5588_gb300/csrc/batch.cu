@@ -41,14 +41,18 @@ struct V16<double> {
   }
 };
 
-// Thread t: sorted row i = t / lr, columns [q W, q W + W) of its k, q = t % lr.
-template <typename TV, typename TX, typename IDX, bool SCATTER>
+// Thread t: sorted row i = t / lr and, of its k columns, the CH 16-byte chunks
+// [q W, q W + W), W = CH * (elements per chunk), q = t % lr (lr = k / W lanes
+// per row). Wider lanes spread the loads of col_start, col and val and the
+// address arithmetic over more fused multiply-adds. Row offsets into X and Y
+// are 32-bit indices widened in the multiply (one wide multiply-add each).
+template <typename TV, typename TX, typename IDX, bool SCATTER, int CH>
 __global__ void __launch_bounds__(BT)
     spmm_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ col_start,
                 const int32_t *__restrict__ block_len, const int32_t *__restrict__ perm, const TX *__restrict__ X,
                 TX *__restrict__ Y, int32_t n_rows, int32_t b, int32_t k, int32_t lr) {
   using TA = typename dev::Acc<TV>::T;
-  constexpr int W = V16<TX>::W, U = 4;
+  constexpr int VW = V16<TX>::W, W = VW * CH, U = 4;
   const int64_t t = (int64_t)blockIdx.x * BT + threadIdx.x;
   const int64_t i = t / lr;
   const int32_t q = (int32_t)(t % lr);
@@ -75,7 +79,10 @@ __global__ void __launch_bounds__(BT)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (c[u] >= 0) {
-        V16<TX>::load(X + (int64_t)c[u] * k + (int64_t)q * W, xv[u]);
+#pragma unroll
+        for (int h = 0; h < CH; ++h)
+          V16<TX>::load(X + (int64_t)c[u] * k + (int64_t)q * W + h * VW,
+                        *reinterpret_cast<TX(*)[VW]>(&xv[u][h * VW]));
       } else {
 #pragma unroll
         for (int w = 0; w < W; ++w) xv[u][w] = TX(0);
@@ -91,7 +98,9 @@ __global__ void __launch_bounds__(BT)
 #pragma unroll
   for (int w = 0; w < W; ++w) out[w] = (TX)acc[w];
   const int64_t r = SCATTER ? (int64_t)__ldcs(perm + i) : i;
-  V16<TX>::store(Y + r * k + (int64_t)q * W, out);
+#pragma unroll
+  for (int h = 0; h < CH; ++h)
+    V16<TX>::store(Y + r * k + (int64_t)q * W + h * VW, *reinterpret_cast<const TX(*)[VW]>(&out[h * VW]));
 }
 
 // ----------------------------------------------------------------------------- persistent batch
@@ -230,10 +239,24 @@ struct pjds_batch {
 
 // ----------------------------------------------------------------------------- spmm
 
+// Chunks per lane, from a GB300 sweep (DLR-like, HMEp-like and Zipf
+// matrices, k = 2..64): two chunks when that still leaves at least 2 lanes
+// per row and n_rows * lanes >= 2^19 threads (DLR-like fp32, k = 32: 1.5x
+// faster than one chunk), one chunk when the longest row has more than 4
+// times the mean length (the longest rows' latency then sets the time and
+// more lanes per row help) or otherwise. Four chunks were within 4% of two
+// at best and are not built.
+static int spmm_chunks(const pjds_dev *A, int32_t k, int vw) {
+  if ((int64_t)A->n_max * A->n_rows > 4 * A->nnz) return 1;
+  const int32_t lanes = k % (2 * vw) == 0 ? k / (2 * vw) : 0;
+  return lanes >= 2 && (int64_t)A->n_rows * lanes >= (1 << 19) ? 2 : 1;
+}
+
 template <typename TV, typename TX>
 static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cudaStream_t s) {
-  constexpr int W = V16<TX>::W;
-  const int32_t lr = k / W;
+  constexpr int VW = V16<TX>::W;
+  const int ch = spmm_chunks(A, k, VW);
+  const int32_t lr = k / (VW * ch);
   const int64_t threads = (int64_t)A->n_rows * lr;
   const int64_t grid = (threads + BT - 1) / BT;
   if (grid <= 0) return PJDS_OK;
@@ -242,16 +265,24 @@ static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cud
   const TX *x = static_cast<const TX *>(X);
   TX *y = static_cast<TX *>(Y);
   const bool small = A->n_stored + A->n_pad < 0x7fffffffLL, sc = !A->permute_cols;
-#define SPMM(IDX, SC)                                                                                       \
-  spmm_kernel<TV, TX, IDX, SC><<<(unsigned)grid, BT, 0, s>>>(val, A->col, A->col_start, A->block_len, A->perm, x, \
-                                                              y, A->n_rows, A->b, k, lr)
+#define SPMM(IDX, SC, CH)                                                                                        \
+  spmm_kernel<TV, TX, IDX, SC, CH><<<(unsigned)grid, BT, 0, s>>>(val, A->col, A->col_start, A->block_len, A->perm, \
+                                                                  x, y, A->n_rows, A->b, k, lr)
+#define SPMM_CH(IDX, SC) \
+  do {                   \
+    if (ch == 2)         \
+      SPMM(IDX, SC, 2);  \
+    else                 \
+      SPMM(IDX, SC, 1);  \
+  } while (0)
   if (small) {
-    if (sc) SPMM(int32_t, true);
-    else SPMM(int32_t, false);
+    if (sc) SPMM_CH(int32_t, true);
+    else SPMM_CH(int32_t, false);
   } else {
-    if (sc) SPMM(int64_t, true);
-    else SPMM(int64_t, false);
+    if (sc) SPMM_CH(int64_t, true);
+    else SPMM_CH(int64_t, false);
   }
+#undef SPMM_CH
 #undef SPMM
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "pjds_spmm launch: %s", cudaGetErrorString(e));

@@ -147,3 +147,33 @@ def test_batch_uneven_matrices(mods, oracle_lib, dtype, graph):
         assert np.array_equal(want, ys[m].cpu().numpy()), m
         assert long_sorted.any() or m == 2
     B.destroy()
+
+
+@pytest.mark.parametrize("dtype,k", [("f32", 16), ("f32", 32), ("f64", 8), ("f64", 16)])
+def test_spmm_two_chunk_lanes(mods, oracle_lib, dtype, k):
+    # 160k rows of 144 entries: enough threads for lanes of two 16-byte chunks;
+    # every column against the oracle, and bit for bit against pjds_spmv
+    torch, pjds, batch = mods
+    A = synth.block_dense(n_brow=40_000, bs=4, nb=36, frac=0.05, seed=11)
+    X = np.random.default_rng(k).uniform(-1, 1, (A.n_cols, k))
+    if dtype != "f64":
+        X = X.astype(np.float32).astype(np.float64)
+    D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype).to_device("cuda")
+    Xt = torch.from_numpy(X).to("cuda", D.vec_dtype).contiguous()
+    Yt = torch.full((A.n_rows, k), float("nan"), dtype=D.vec_dtype, device="cuda")
+    batch.spmm(D, Xt, Yt)
+    torch.cuda.synchronize()
+    Ar = A if dtype == "f64" else A._replace(val=oracle_lib.round_f32(A.val))
+    Yr = oracle_lib.crs_spmm(Ar, X)
+    S = oracle_lib.crs_spmm(Ar._replace(val=np.abs(Ar.val)), np.abs(X))
+    Y = Yt.double().cpu().numpy()
+    check = parity.check_fp64 if dtype == "f64" else parity.check_fp32
+    lens = np.diff(A.row_ptr)
+    for c in range(k):
+        r = check(Y[:, c], Yr[:, c], S[:, c], lens)
+        assert r["ok"], (c, r)
+    for c in range(k):
+        y1 = torch.empty(A.n_rows, dtype=D.vec_dtype, device="cuda")
+        pjds.pjds_spmv_cfg(D, Xt[:, c].contiguous(), y1, threads_per_row=1, rows_per_thread=1, tile_order=-1)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, Yt[:, c].contiguous()), c
