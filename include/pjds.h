@@ -242,6 +242,24 @@ int pjds_wait_selftest(int32_t which, void *stream);
 int pjds_spmv_host(const pjds_dev *A, const void *x_host, void *y_host, void *x_dev, void *y_dev, void *stream);
 
 /*
+ * A stream of independent products from host memory: y_v = A x_v for
+ * v < n_vec, x_host[v] holding n_cols and y_host[v] n_rows elements of A's
+ * vector type (pinned host memory for full link bandwidth; the same host
+ * buffer may appear more than once). x_dev[0..1] and y_dev[0..1] are two
+ * caller-owned device buffers each (four distinct buffers), used in turn:
+ * while product v runs on `stream`, x_{v+1} is copied in and y_{v-1} copied
+ * out on two copy streams the call creates and orders with events. Eq. 2
+ * adds the transfer time T_PCI to the product time T_MVM; here the two
+ * overlap as far as the host link allows. Work already queued on `stream`
+ * runs first; the call returns when every y_host[v] is written. Same mapping
+ * and results as pjds_spmv. The paper has no counterpart of this call.
+ * Errors: PJDS_EINVAL (n_vec < 0, a NULL pointer, a device buffer reused),
+ * PJDS_ECUDA.
+ */
+int pjds_spmv_host_stream(const pjds_dev *A, int32_t n_vec, const void *const *x_host, void *const *y_host,
+                          void *const *x_dev, void *const *y_dev, void *stream);
+
+/*
  * Basis changes around an iterative solver (Sect. 2.1): for i < n_rows,
  *   pjds_permute:   v_perm[i] = v[perm[i]]   (original -> permuted basis)
  *   pjds_unpermute: v[perm[i]] = v_perm[i]   (permuted -> original basis)

@@ -197,6 +197,74 @@ extern "C" int pjds_spmv_host(const pjds_dev *A, const void *x_host, void *y_hos
   return PJDS_OK;
 }
 
+extern "C" int pjds_spmv_host_stream(const pjds_dev *A, int32_t n_vec, const void *const *x_host,
+                                     void *const *y_host, void *const *x_dev, void *const *y_dev, void *stream) {
+  clear_error();
+  if (n_vec < 0) return set_error(PJDS_EINVAL, "n_vec = %d", n_vec);
+  if (!x_host || !y_host || !x_dev || !y_dev) return set_error(PJDS_EINVAL, "a pointer array is NULL");
+  int rc = check_pjds_dev(A, x_dev[0], y_dev[0]);
+  if (rc) return rc;
+  if ((rc = check_pjds_dev(A, x_dev[1], y_dev[1]))) return rc;
+  if (A->n_rows > 0) {
+    const void *d[4] = {x_dev[0], x_dev[1], y_dev[0], y_dev[1]};
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (d[a] == d[b]) return set_error(PJDS_EINVAL, "the four device buffers must be distinct");
+    for (int32_t v = 0; v < n_vec; ++v)
+      if (!x_host[v] || !y_host[v]) return set_error(PJDS_EINVAL, "host vector %d is NULL", v);
+  }
+  LaunchCfg c = default_cfg(A);
+  if ((rc = check_cfg(A, c))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_vec == 0 || A->n_rows == 0) {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+  }
+  const size_t vb = (size_t)vector_bytes(A->dtype), nx = (size_t)A->n_cols * vb, ny = (size_t)A->n_rows * vb;
+  cudaStream_t cin = nullptr, cout = nullptr;
+  // start, done, and per buffer: x ready, product done, y copied out
+  cudaEvent_t ev[8] = {};
+  cudaError_t e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
+  for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+  cudaEvent_t start = ev[0], done = ev[1], *xr = ev + 2, *kd = ev + 4, *yo = ev + 6;
+  if (e == cudaSuccess) e = cudaEventRecord(start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, start, 0);
+  for (int32_t v = 0; v < n_vec && e == cudaSuccess && rc == PJDS_OK; ++v) {
+    const int b = v & 1;
+    if (v >= 2) e = cudaStreamWaitEvent(cin, kd[b], 0);  // x buffer b: product v-2 has read it
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x_dev[b], x_host[v], nx, cudaMemcpyHostToDevice, cin);
+    if (e == cudaSuccess) e = cudaEventRecord(xr[b], cin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, xr[b], 0);
+    if (e == cudaSuccess && v >= 2) e = cudaStreamWaitEvent(s, yo[b], 0);  // y buffer b: y_{v-2} is out
+    if (e != cudaSuccess) break;
+    rc = dispatch_pjds(A, x_dev[b], y_dev[b], c, s);
+    if (rc) break;
+    e = cudaEventRecord(kd[b], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, kd[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_host[v], y_dev[b], ny, cudaMemcpyDeviceToHost, cout);
+    if (e == cudaSuccess) e = cudaEventRecord(yo[b], cout);
+  }
+  if (e == cudaSuccess && rc == PJDS_OK) e = cudaEventRecord(done, cout);
+  if (e == cudaSuccess && rc == PJDS_OK) e = cudaStreamWaitEvent(s, done, 0);
+  // drain every stream before releasing them, on success and on error alike
+  cudaError_t es = cudaStreamSynchronize(s);
+  if (cin) cudaStreamSynchronize(cin);
+  if (cout) {
+    const cudaError_t eo = cudaStreamSynchronize(cout);
+    if (es == cudaSuccess) es = eo;
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  if (cin) cudaStreamDestroy(cin);
+  if (cout) cudaStreamDestroy(cout);
+  if (rc) return rc;
+  if (e != cudaSuccess) return set_error(PJDS_ECUDA, "host stream: %s", cudaGetErrorString(e));
+  if (es != cudaSuccess) return set_error(PJDS_ECUDA, "host stream synchronize: %s", cudaGetErrorString(es));
+  return PJDS_OK;
+}
+
 static int permute_common(const pjds_dev *A, const void *src, void *dst, bool inverse, void *stream) {
   clear_error();
   if (!A) return set_error(PJDS_EINVAL, "A is NULL");

@@ -82,6 +82,7 @@ def _load_lib():
         "pjds_spmv": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_spmv_cfg": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, P(_LaunchS), _vp]),
         "pjds_spmv_host": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp, _vp, _vp]),
+        "pjds_spmv_host_stream": (ctypes.c_int, [P(_PjdsDevS), _i32, P(_vp), P(_vp), P(_vp), P(_vp), _vp]),
         "pjds_spmv_resolve": (ctypes.c_int, [P(_PjdsDevS), P(_LaunchS), P(_LaunchS)]),
         "pjds_device_status": (ctypes.c_int, [P(_i32), _i32, _vp]),
         "pjds_wait_selftest": (ctypes.c_int, [_i32, _vp]),
@@ -320,6 +321,31 @@ def pjds_spmv_host(A: PjdsDevice, x_host: torch.Tensor, y_host: torch.Tensor, x_
     _check(_lib.pjds_spmv_host(ctypes.byref(A.struct), x_host.data_ptr(), y_host.data_ptr(), x_dev.data_ptr(),
                                y_dev.data_ptr(), _stream_ptr(stream)), "pjds_spmv_host")
     return y_host
+
+
+def pjds_spmv_host_stream(A: PjdsDevice, xs_host, ys_host, x_dev, y_dev, stream=None):
+    """y_v = A x_v for a list of host vectors, copies overlapped with the
+    products (pjds_spmv_host_stream). x_dev, y_dev: two device buffers each."""
+    if len(xs_host) != len(ys_host):
+        raise ValueError("xs_host and ys_host must have the same length")
+    for lst, n, name in ((xs_host, A.n_cols, "x_host"), (ys_host, A.n_rows, "y_host")):
+        for t in lst:
+            if t.device.type != "cpu" or t.dtype != A.vec_dtype or t.numel() != n or not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous CPU {A.vec_dtype} tensors with {n} elements")
+    if len(x_dev) != 2 or len(y_dev) != 2:
+        raise ValueError("x_dev and y_dev must hold two device buffers each")
+    for t in x_dev:
+        _check_vec(t, A.n_cols, A.vec_dtype, "x_dev")
+    for t in y_dev:
+        _check_vec(t, A.n_rows, A.vec_dtype, "y_dev")
+    n = len(xs_host)
+    xp = (_vp * max(n, 1))(*[t.data_ptr() for t in xs_host])
+    yp = (_vp * max(n, 1))(*[t.data_ptr() for t in ys_host])
+    xd = (_vp * 2)(*[t.data_ptr() for t in x_dev])
+    yd = (_vp * 2)(*[t.data_ptr() for t in y_dev])
+    _check(_lib.pjds_spmv_host_stream(ctypes.byref(A.struct), n, xp, yp, xd, yd, _stream_ptr(stream)),
+           "pjds_spmv_host_stream")
+    return ys_host
 
 
 def pjds_permute(A: PjdsDevice, v: torch.Tensor, v_perm: torch.Tensor, stream=None) -> torch.Tensor:

@@ -284,3 +284,21 @@ def test_tile_order_definition(P, b):
         k = key[H.tile_order]
         assert np.all(k[1:] >= k[:-1])
         H.destroy()
+
+
+def test_host_stream_argument_checks_without_gpu(P):
+    # rejected on the host before any CUDA call (the device pointers are never used)
+    A = tiny.random_lengths(64, 64, max_len=8, seed=1)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    s = P._dev_struct_from_host(H)
+    lib, V, ref = P.lib(), ctypes.c_void_p, ctypes.byref
+    xd, yd = (V * 2)(1024, 2048), (V * 2)(4096, 8192)
+    xh, yh = (V * 1)(1 << 20), (V * 1)(1 << 21)
+    assert lib.pjds_spmv_host_stream(ref(s), -1, xh, yh, xd, yd, None) == -1
+    assert lib.pjds_spmv_host_stream(ref(s), 1, None, yh, xd, yd, None) == -1
+    assert lib.pjds_spmv_host_stream(ref(s), 1, xh, yh, (V * 2)(1024, 1024), yd, None) == -1
+    assert lib.pjds_spmv_host_stream(ref(s), 1, xh, yh, xd, (V * 2)(4096, 1024), None) == -1
+    assert lib.pjds_spmv_host_stream(ref(s), 1, (V * 1)(None), yh, xd, yd, None) == -1
+    assert lib.pjds_spmv_host_stream(ref(s), 1, xh, yh, (V * 2)(None, 2048), yd, None) == -1
+    assert lib.pjds_spmv_host_stream(ref(s), 1, xh, yh, (V * 2)(8, 8), yd, None) == -1
+    assert b"distinct" in lib.pjds_last_error()

@@ -307,3 +307,26 @@ def test_tile_order_entry_out_of_range_is_skipped(P):
         torch.cuda.synchronize()
         assert torch.isnan(y[skipped]).all(), cfg
         assert torch.equal(y[~skipped], ref[~skipped]), cfg
+
+
+@pytest.mark.parametrize("dtype,permute", [("f64", False), ("f32", True), ("bf16", False)])
+def test_host_stream_equals_single_products(P, dtype, permute):
+    # overlapped host stream: every y_v bit for bit the device product of x_v
+    torch = _torch()
+    A = synth.hmep_like(n=50_000, seed=61)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype, permute_cols=permute)
+    D = H.to_device("cuda")
+    n_vec = 5
+    xs = [torch.from_numpy(synth.vector(A.n_cols, seed=70 + v)).to(D.vec_dtype).pin_memory() for v in range(n_vec)]
+    xs.append(xs[1])  # a host buffer may repeat
+    ys = [torch.full((A.n_rows,), float("nan"), dtype=D.vec_dtype).pin_memory() for _ in xs]
+    xd = [torch.empty(A.n_cols, dtype=D.vec_dtype, device="cuda") for _ in range(2)]
+    yd = [torch.empty(A.n_rows, dtype=D.vec_dtype, device="cuda") for _ in range(2)]
+    P.pjds_spmv_host_stream(D, xs, ys, xd, yd)
+    for v, (xh, yh) in enumerate(zip(xs, ys)):
+        ref = torch.empty(A.n_rows, dtype=D.vec_dtype, device="cuda")
+        P.pjds_spmv(D, xh.cuda(), ref)
+        torch.cuda.synchronize()
+        assert torch.equal(ref.cpu(), yh), v
+    # nothing to do: returns at once
+    P.pjds_spmv_host_stream(D, [], [], xd, yd)
