@@ -328,11 +328,37 @@ def run_ours(args, world, rank, local_rank):
         cpu = {"value": round(nbytes * reps / t_cpu / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"full matrix ({A.nnz} nnz), {reps} CRS products in {t_cpu:.1f} s",
                "gflops": round(2 * A.nnz * reps / t_cpu / 1e9, 3)}
+        # the same on one core (a few seconds)
+        oracle.set_threads(1)
+        reps1, t1 = 0, 0.0
+        while t1 < max(1.0, args.cpu_seconds / 4) and reps1 < 100:
+            t0 = time.perf_counter()
+            oracle.crs_spmv(A, x)
+            t1 += time.perf_counter() - t0
+            reps1 += 1
+        oracle.set_threads(cores)
+        cpu["one_core"] = {"value": round(nbytes * reps1 / t1 / 1e9, 3), "unit": "GB/s",
+                           "gflops": round(2 * A.nnz * reps1 / t1 / 1e9, 3), "products": reps1}
         absax = oracle.crs_absmv(A, x)
         err = float(np.max(np.abs(y_gpu - y_ref)) / np.max(absax))
         if prec_gpu is not None:
             prec_gpu = precision_oracle_checks(oracle, prec_gpu)
 
+    # the paper's model (Eqs. 1-2) with this GPU's measured bandwidths
+    from paper_1112_5588_gb300 import perfmodel as pm
+    n_nzr = A.nnz / A.n_rows
+    t_single = nbytes / e2e_single_rate  # seconds per single-call product
+    t_kernel = per_launch
+    model = {"n_nzr": round(n_nzr, 3),
+             "code_balance_bytes_per_flop": {"alpha_1_over_nnzr": round(pm.code_balance(1 / n_nzr, n_nzr), 3),
+                                             "alpha_1": round(pm.code_balance(1.0, n_nzr), 3)},
+             "roofline_gflops_at_peak": {"alpha_1_over_nnzr": round(pm.roofline_gflops(peak, 1 / n_nzr, n_nzr), 1),
+                                         "alpha_1": round(pm.roofline_gflops(peak, 1.0, n_nzr), 1)},
+             "achieved_gflops": round(2 * A.nnz / t_kernel / 1e9, 1),
+             "t_mvm_model_us": round(pm.t_mvm(A.n_rows, n_nzr, 1 / n_nzr, peak * 1e9) * 1e6, 1),
+             "t_mvm_measured_us": round(t_kernel * 1e6, 1),
+             "t_pci_measured_us": round((t_single - t_kernel) * 1e6, 1),
+             "b_pci_effective_gbs": round(16 * A.n_rows / (t_single - t_kernel) / 1e9, 1) if t_single > t_kernel else None}
     src_hash = kernel_source_hash()
     launched = pjds.pjds_spmv_resolve(D)
     tr = NCU_TRAFFIC.get(("hmep_f64_pjds", A.n_rows))
@@ -356,6 +382,7 @@ def run_ours(args, world, rank, local_rank):
                 "single_call_value": round(e2e_single_rate / 1e9, 3),
                 "single_call_api": "pjds_spmv_host (copy in, product, copy out per call)"},
         "gpu_launches": gpu_launches,
+        "perf_model": model,
         "clocks": clk.summary(),
         "error_fp64_normwise": err,
         "setup_s": {"generate": round(t_gen, 2), "pjds_create": round(t_conv, 2)},

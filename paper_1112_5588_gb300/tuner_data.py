@@ -5,6 +5,7 @@ Run on a GPU:
     python -m paper_1112_5588_gb300.tuner_data generate --n-train 800 --n-test 200 --out timings.npz
     python -m paper_1112_5588_gb300.tuner_data train timings.npz --model tuner_mlp.json
     python -m paper_1112_5588_gb300.tuner_data evaluate timings.npz --model tuner_mlp.json
+    python -m paper_1112_5588_gb300.tuner_data recheck timings.npz --model tuner_mlp.json --count 200
 
 `generate` draws seeded synthetic matrices (N log-uniform, Zipf(s) row
 lengths with s uniform in [1.5, 3] and a cap drawn from {64, ..., 1024},
@@ -15,7 +16,11 @@ sweep. `train` fits the cost model (log of the kernel time) on the training
 matrices in libpjds's CUDA kernels. `evaluate` reports the regret of the
 model's choice against the sweep's best on the held-out matrices, for each
 precision separately (the precision is the caller's choice; the tuner picks b
-and threads per row within it) and over all candidates.
+and threads per row within it) and over all candidates. `recheck` rebuilds
+the first `--count` held-out matrices from their stored parameters, times
+the candidate space again with the library as it is now, and reports the
+model's regret on those fresh timings and their agreement with the stored
+ones (the model is not retrained).
 """
 from __future__ import annotations
 
@@ -125,6 +130,38 @@ def evaluate(data: dict, m) -> dict:
     return out
 
 
+def recheck(data: dict, m, count: int, reps: int = 3, log=sys.stderr) -> dict:
+    """Fresh sweep of held-out matrices; regret of `m` on the new timings."""
+    from . import tune
+    cands = json.loads(str(data["cands"]))
+    n_train = int(data["n_train"])
+    params = json.loads(str(data["params"]))
+    rows = list(range(n_train, min(len(params), n_train + count)))
+    fresh = {k: np.asarray(v).copy() for k, v in data.items()}
+    ratios = []
+    t0 = time.time()
+    for k, i in enumerate(rows):
+        A = make_matrix(params[i])
+        entries, _ = tune.sweep(A, cands, reps=reps, flush_bytes=0)
+        t = np.full(len(cands), np.nan)
+        for c, e in enumerate(entries):
+            if e["status"] == 0 and e["us"] > 0:
+                t[c] = e["us"]
+        old = data["times_us"][i]
+        ok = np.isfinite(t) & np.isfinite(old)
+        ratios.extend((t[ok] / old[ok]).tolist())
+        fresh["times_us"][i] = t
+        if (k + 1) % 50 == 0:
+            print(f"[tuner_data] recheck {k + 1}/{len(rows)}, {time.time() - t0:.0f} s", file=log, flush=True)
+    fresh["times_us"] = fresh["times_us"][: n_train + len(rows)]
+    fresh["features"] = fresh["features"][: n_train + len(rows)]
+    r = np.array(ratios)
+    return {"matrices": len(rows), "new_over_stored_time": {"median": float(np.median(r)),
+                                                             "p10": float(np.percentile(r, 10)),
+                                                             "p90": float(np.percentile(r, 90))},
+            "regret_on_fresh_timings": evaluate(fresh, m)}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -144,6 +181,10 @@ def main(argv=None) -> int:
     e = sub.add_parser("evaluate")
     e.add_argument("data")
     e.add_argument("--model", required=True)
+    r = sub.add_parser("recheck")
+    r.add_argument("data")
+    r.add_argument("--model", required=True)
+    r.add_argument("--count", type=int, default=200)
     a = ap.parse_args(argv)
     if a.cmd == "generate":
         d = generate(a.n_train, a.n_test, a.seed, a.n_lo, a.n_hi)
@@ -158,6 +199,10 @@ def main(argv=None) -> int:
                                   "data": a.data, "heldout": ev})
         print(json.dumps({"model": a.model, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
                           "heldout": ev}))
+    elif a.cmd == "recheck":
+        from . import learned
+        d = dict(np.load(a.data, allow_pickle=False))
+        print(json.dumps(recheck(d, learned.load(a.model), a.count)))
     else:
         from . import learned
         d = dict(np.load(a.data, allow_pickle=False))
