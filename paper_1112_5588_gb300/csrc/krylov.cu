@@ -201,14 +201,48 @@ __global__ void __launch_bounds__(KT) sumsq_kernel(const TX *__restrict__ v, Fin
   finish(s, f);
 }
 
-// d += alpha p; r -= alpha q; reduces sum r_i^2
+// 16-byte groups of workspace vectors (the workspace is 256-byte aligned):
+// W elements per load and store.
+template <typename TX>
+struct G16 {
+  static constexpr int W = 16 / (int)sizeof(TX);
+  __device__ static void load(const TX *p, TX (&v)[W]) {
+    const uint4 u = *reinterpret_cast<const uint4 *>(p);
+    memcpy(v, &u, 16);
+  }
+  __device__ static void store(TX *p, const TX (&v)[W]) {
+    uint4 u;
+    memcpy(&u, v, 16);
+    *reinterpret_cast<uint4 *>(p) = u;
+  }
+};
+
+// d += alpha p; r -= alpha q; reduces sum r_i^2. Thread k takes 16-byte
+// groups k, k + stride, ...; the last n mod W elements go one per thread.
 template <typename TX>
 __global__ void __launch_bounds__(KT)
     cg_update_kernel(TX *__restrict__ d, TX *__restrict__ r, const TX *__restrict__ p, const TX *__restrict__ q,
                      Fin f, int32_t n) {
+  constexpr int W = G16<TX>::W;
   const TX a = (TX)f.scal[S_ALPHA];
+  const int64_t ng = n / W, stride = (int64_t)gridDim.x * KT, t = (int64_t)blockIdx.x * KT + threadIdx.x;
   double contrib = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
+  for (int64_t k = t; k < ng; k += stride) {
+    TX dv[W], rv[W], pv[W], qv[W];
+    G16<TX>::load(d + k * W, dv);
+    G16<TX>::load(r + k * W, rv);
+    G16<TX>::load(p + k * W, pv);
+    G16<TX>::load(q + k * W, qv);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      dv[w] = dv[w] + a * pv[w];
+      rv[w] = rv[w] - a * qv[w];
+      contrib += (double)rv[w] * (double)rv[w];
+    }
+    G16<TX>::store(d + k * W, dv);
+    G16<TX>::store(r + k * W, rv);
+  }
+  for (int64_t i = ng * W + t; i < n; i += stride) {
     d[i] = d[i] + a * p[i];
     const TX ri = r[i] - a * q[i];
     r[i] = ri;
@@ -218,12 +252,24 @@ __global__ void __launch_bounds__(KT)
   finish(s, f);
 }
 
-// p = r + beta p
+// p = r + beta p: one 16-byte group per thread, then the last n mod W
+// elements one per thread.
 template <typename TX>
 __global__ void __launch_bounds__(KT)
     cg_dir_kernel(TX *__restrict__ p, const TX *__restrict__ r, const double *__restrict__ scal, int32_t n) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
-  if (i < n) p[i] = r[i] + (TX)scal[S_BETA] * p[i];
+  constexpr int W = G16<TX>::W;
+  const TX be = (TX)scal[S_BETA];
+  const int64_t ng = n / W, k = (int64_t)blockIdx.x * KT + threadIdx.x;
+  if (k < ng) {
+    TX pv[W], rv[W];
+    G16<TX>::load(p + k * W, pv);
+    G16<TX>::load(r + k * W, rv);
+#pragma unroll
+    for (int w = 0; w < W; ++w) pv[w] = rv[w] + be * pv[w];
+    G16<TX>::store(p + k * W, pv);
+  }
+  const int64_t i = ng * W + k;
+  if (i < n) p[i] = r[i] + be * p[i];
 }
 
 // Start of an inner solve: r = p = (r64 / ||r64||) in the inner type, d = 0,
@@ -271,9 +317,24 @@ __global__ void __launch_bounds__(KT)
     lanczos_orth_kernel(TX *__restrict__ w, const TX *__restrict__ v, const TX *__restrict__ vprev,
                         const double *__restrict__ alpha, const double *__restrict__ beta, int32_t j, Fin f,
                         int32_t n) {
+  constexpr int W = G16<TX>::W;
   const double aj = alpha[j], bj = beta[j];
+  const int64_t ng = n / W, stride = (int64_t)gridDim.x * KT, t = (int64_t)blockIdx.x * KT + threadIdx.x;
   double contrib = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
+  for (int64_t k = t; k < ng; k += stride) {
+    TX wv[W], vv[W], pv[W];
+    G16<TX>::load(w + k * W, wv);
+    G16<TX>::load(v + k * W, vv);
+    G16<TX>::load(vprev + k * W, pv);
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      const TX ws = (TX)((double)wv[e] - aj * (double)vv[e] - bj * (double)pv[e]);
+      wv[e] = ws;
+      contrib += (double)ws * (double)ws;
+    }
+    G16<TX>::store(w + k * W, wv);
+  }
+  for (int64_t i = ng * W + t; i < n; i += stride) {
     const double wi = (double)w[i] - aj * (double)v[i] - bj * (double)vprev[i];
     const TX ws = (TX)wi;
     w[i] = ws;
@@ -288,12 +349,32 @@ template <typename TX>
 __global__ void __launch_bounds__(KT)
     lanczos_next_kernel(TX *__restrict__ vprev, TX *__restrict__ v, const TX *__restrict__ w,
                         const double *__restrict__ scal, TX *__restrict__ basis_row, int32_t n) {
-  const int64_t i = (int64_t)blockIdx.x * KT + threadIdx.x;
+  constexpr int W = G16<TX>::W;
+  const double inv = scal[S_INVNRM];
+  const int64_t ng = n / W, k = (int64_t)blockIdx.x * KT + threadIdx.x;
+  // the basis row is caller memory: 16-byte stores only when it is aligned
+  const bool row16 = basis_row && ((uintptr_t)basis_row & 15) == 0;
+  if (k < ng) {
+    TX vv[W], wv[W], nv[W];
+    G16<TX>::load(v + k * W, vv);
+    G16<TX>::load(w + k * W, wv);
+    if (row16) {
+      G16<TX>::store(basis_row + k * W, vv);
+    } else if (basis_row) {
+#pragma unroll
+      for (int e = 0; e < W; ++e) basis_row[k * W + e] = vv[e];
+    }
+    G16<TX>::store(vprev + k * W, vv);
+#pragma unroll
+    for (int e = 0; e < W; ++e) nv[e] = (TX)((double)wv[e] * inv);
+    G16<TX>::store(v + k * W, nv);
+  }
+  const int64_t i = ng * W + k;
   if (i < n) {
     const TX vi = v[i];
     if (basis_row) basis_row[i] = vi;
     vprev[i] = vi;
-    v[i] = (TX)((double)w[i] * scal[S_INVNRM]);
+    v[i] = (TX)((double)w[i] * inv);
   }
 }
 
@@ -471,6 +552,9 @@ static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, doubl
   if ((rc = make_dot(Al, &dot_lo)) || (rc = make_dot(Ah, &dot_res)) || (rc = red_grid(sumsq_kernel<double>, n, &g_sumsq)) ||
       (rc = red_grid(cg_update_kernel<TL>, n, &g_upd)) || (rc = red_grid(ir_start_kernel<TL>, n, &g_start)))
     return rc;
+  // cg_dir: one thread per 16-byte group, and as many for the remainder
+  const int64_t n_groups = n / G16<TL>::W, n_rem = n - n_groups * G16<TL>::W;
+  const int32_t nb_dir = (int32_t)((std::max<int64_t>(std::max(n_groups, n_rem), 1) + KT - 1) / KT);
 
   // scalar block and reduction counter start at 0
   cudaError_t e = cudaMemsetAsync(scal, 0, S_COUNT * sizeof(double), s);
@@ -487,7 +571,7 @@ static int cg_run(const pjds_dev *Ah, const pjds_dev *Al, const double *b, doubl
   auto inner_step = [&](cudaStream_t st) {
     launch_dot(dot_lo, Al, p, q, nullptr, fin(F_ALPHA, 0), st);                  // q = A p, (p, q), alpha
     cg_update_kernel<TL><<<g_upd, KT, 0, st>>>(d, r, p, q, fin(F_BETA, 0), n);  // d, r, (r, r), beta
-    cg_dir_kernel<TL><<<nb, KT, 0, st>>>(p, r, scal, n);                        // p
+    cg_dir_kernel<TL><<<nb_dir, KT, 0, st>>>(p, r, scal, n);                    // p
   };
 
   cudaGraphExec_t exec = nullptr;
@@ -603,6 +687,9 @@ static int lanczos_run(const pjds_dev *A, const TX *v0, int32_t steps, double *a
   if ((rc = make_dot(A, &dot)) || (rc = red_grid(sumsq_kernel<TX>, n, &g_sumsq)) ||
       (rc = red_grid(lanczos_orth_kernel<TX>, n, &g_orth)))
     return rc;
+  // lanczos_next: one thread per 16-byte group, and as many for the remainder
+  const int64_t n_groups = n / G16<TX>::W, n_rem = n - n_groups * G16<TX>::W;
+  const int32_t nb_next = (int32_t)((std::max<int64_t>(std::max(n_groups, n_rem), 1) + KT - 1) / KT);
   sumsq_kernel<TX><<<g_sumsq, KT, 0, s>>>(v0, Fin{partial, scal, nullptr, F_NORM, 0}, n);
   lanczos_start_kernel<TX><<<nb, KT, 0, s>>>(v0, v, vp, scal, n);
   rc = launch_check("lanczos start");
@@ -611,7 +698,7 @@ static int lanczos_run(const pjds_dev *A, const TX *v0, int32_t steps, double *a
     launch_dot(dot, A, v, w, nullptr, Fin{partial, scal, alpha, F_LALPHA, j}, st);  // w = A v, alpha_j = (v, w)
     lanczos_orth_kernel<TX>
         <<<g_orth, KT, 0, st>>>(w, v, vp, alpha, beta, j, Fin{partial, scal, beta, F_LBETA, j + 1}, n);  // beta_j+1
-    lanczos_next_kernel<TX><<<nb, KT, 0, st>>>(vp, v, w, scal, basis ? basis + (int64_t)j * n : nullptr, n);
+    lanczos_next_kernel<TX><<<nb_next, KT, 0, st>>>(vp, v, w, scal, basis ? basis + (int64_t)j * n : nullptr, n);
   };
   if (use_graph) {
     cudaGraphExec_t exec = nullptr;

@@ -157,3 +157,29 @@ def test_lanczos_low_precision_with_fp64_ritz_refinement(mods, oracle_lib, dtype
     yo[perm] = y.cpu().numpy()
     r_or = np.linalg.norm(oracle_lib.crs_spmv(A, yo) - th_ref64 * yo) / np.linalg.norm(yo) / abs(th_ref64)
     assert resid == pytest.approx(r_or, rel=1e-6, abs=1e-14)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_lanczos_basis_rows_of_odd_length(mods, oracle_lib, dtype):
+    # n = 17^3 = 4913: basis row j starts j * n elements in, so most rows are
+    # not 16-byte aligned and take the element-wise stores; keeping the basis
+    # changes no arithmetic, and the stored rows are the Lanczos vectors
+    torch, pjds, krylov = mods
+    from oracle import krylov as ok
+    A = synth.stencil27(g=17, seed=5)
+    assert A.n_rows % 2 == 1
+    v0 = synth.vector(A.n_rows, seed=9)
+    D, perm = _dev(pjds, A, dtype)
+    v0t = torch.from_numpy(v0[perm]).to("cuda", D.vec_dtype)
+    k = 30
+    a1, b1, V = krylov.lanczos(D, v0t, k, keep_basis=True)
+    a2, b2, _ = krylov.lanczos(D, v0t, k, keep_basis=False)
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    Vh = V.double().cpu().numpy()
+    v0n = v0t.double().cpu().numpy()
+    assert np.allclose(Vh[0], v0n / np.linalg.norm(v0n), rtol=0, atol=1e-6 if dtype == "f32" else 1e-15)
+    G = Vh[:8] @ Vh[:8].T
+    assert np.allclose(G, np.eye(8), atol=1e-5 if dtype == "f32" else 1e-10)
+    if dtype == "f64":
+        ra, rb, _ = ok.lanczos(A, v0, k)
+        assert np.allclose(a1[:10], ra[:10], rtol=1e-10, atol=0)
