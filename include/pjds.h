@@ -154,8 +154,10 @@ int pjds_destroy(pjds_host *h);
  * and every row is shorter than 64; otherwise T = 2, 4 or 8 threads share a
  * row (each sums every T-th entry in order, then a fixed shuffle tree adds
  * the T partial sums), T being the smallest with n_rows * T reaching that
- * thread count, and at least 2 for rows of 64 entries or more.
- * pjds_spmv_resolve reports the mapping chosen for a matrix.
+ * thread count, and at least 2 for rows of 64 entries or more. With one
+ * thread per row, fp32 and bf16 values from 2^21 rows on take two adjacent
+ * rows per thread (same per-row arithmetic) when val and col allow the
+ * paired loads. pjds_spmv_resolve reports the mapping chosen for a matrix.
  */
 int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
 

@@ -227,6 +227,27 @@ def test_resolve_defaults(P):
     assert P.pjds_spmv_resolve(HL)["threads_per_row"] == 2
 
 
+def test_resolve_large_matrix_defaults(P):
+    # one thread per row from 2^19 (fp64) / 2^20 rows: 256-thread CTAs, and two
+    # rows per thread for fp32 / bf16 values from 2^21 rows on
+    C = _band(1 << 21, 3)
+    for dt, R in (("f64", 1), ("f32", 2), ("bf16", 2)):
+        H = P.pjds_create(C.n_rows, C.n_cols, C.row_ptr, C.col, C.val, b=32, dtype=dt)
+        r = P.pjds_spmv_resolve(H)
+        assert (r["threads_per_row"], r["rows_per_thread"], r["block_threads"], r["unroll"]) == (1, R, 256, 4), (dt, r)
+        # asking for several threads per row implies one row per thread
+        assert P.pjds_spmv_resolve(H, threads_per_row=2)["rows_per_thread"] == 1
+        s = P._dev_struct_from_host(H)
+        s.val = 514  # not aligned for paired loads: one row per thread
+        out = P._LaunchS()
+        assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(out)) == 0
+        assert out.rows_per_thread == 1
+        H.destroy()
+    C = _band((1 << 21) - 1, 3)
+    H = P.pjds_create(C.n_rows, C.n_cols, C.row_ptr, C.col, C.val, b=32, dtype="f32")
+    assert P.pjds_spmv_resolve(H)["rows_per_thread"] == 1
+
+
 def test_resolve_tile_order_rule(P):
     # automatic: the traversal table from 2^20 rows on when the longest row is
     # at most 4 times the mean row length; 1 / -1 force it on / off
