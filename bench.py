@@ -636,9 +636,14 @@ def batching_leg(torch, pjds, args, dev, flush):
     del D
     rng = np.random.default_rng(args.seed)
     sizes = np.exp(rng.uniform(np.log(10_000), np.log(500_000), 64)).astype(int)
-    devs, xs, ys, nnz, nbytes = [], [], [], 0, 0
+    from paper_1112_5588_gb300 import learned
+    model = learned.load()
+    cands = [{"b": 32, "dtype": "f64", "rows_per_thread": 0, "threads_per_row": t, "block_threads": 0, "unroll": 0}
+             for t in (1, 2, 4, 8)]
+    devs, xs, ys, nnz, nbytes, tuned = [], [], [], 0, 0, []
     for m, n in enumerate(sizes):
         M = synth.zipf_rows(int(n), s=2.0, len_max=512, seed=args.seed + m)
+        tuned.append(learned.choose(M, cands, model=model)[1]["threads_per_row"])
         Hm = pjds.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32, dtype="f64")
         devs.append(Hm.to_device(dev))
         Hm.destroy()
@@ -671,6 +676,21 @@ def batching_leg(torch, pjds, args, dev, flush):
                            "speedup_vs_separate": round(t_sep / t_batch, 3),
                            "speedup_vs_separate_graph": round(t_sep_graph / t_batch, 3)}
     B.destroy()
+    # tiles with the learned tuner's threads per row for each matrix
+    Bt = batch.Batch(devs, xs, ys, lanes=tuned)
+    t_tuned = statistics.median(time_launches(torch, lambda: Bt.run(use_graph=True), 10, 3, flush))
+    out["multi_matrix"]["tuned_lanes_graph_us"] = round(t_tuned * 1e6, 2)
+    out["multi_matrix"]["tuned_lanes_histogram"] = {str(t): int(sum(1 for v in tuned if v == t)) for t in (1, 2, 4, 8)}
+    Bt.destroy()
+    # the batch's own autotuner: exhaustive sweep of block-length tile rules
+    best, timings = batch.tune_rule(devs, xs, ys, reps=5)
+    Br = batch.Batch(devs, xs, ys, rule=best)
+    t_rule = statistics.median(time_launches(torch, lambda: Br.run(use_graph=True), 10, 3, flush))
+    Br.destroy()
+    out["multi_matrix"]["rule_sweep_us"] = {",".join("-" if v == batch.NEVER else str(v) for v in r): round(u, 1)
+                                            for r, u in timings}
+    out["multi_matrix"]["tuned_rule"] = list(best)
+    out["multi_matrix"]["tuned_rule_graph_us"] = round(t_rule * 1e6, 2)
     del devs, xs, ys
     torch.cuda.empty_cache()
     return out

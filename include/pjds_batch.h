@@ -67,6 +67,44 @@ int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const void *const *x
                       void *plan_dev, size_t plan_bytes, pjds_batch **out, void *stream);
 
 /*
+ * pjds_batch_create with the lanes per row of each matrix given: lanes[m] in
+ * {1, 2, 4, 8} cuts every tile of matrix m to 256 / lanes[m] rows with that
+ * many lanes per row (the threads_per_row an autotuner chose for the matrix,
+ * pjds_tune.h / pjds_mlp.h); 0 keeps the rule above. lanes = NULL is
+ * pjds_batch_create. A row taken by T lanes gives the same bits as
+ * pjds_spmv_cfg with threads_per_row = T. Errors as pjds_batch_create, and
+ * PJDS_EINVAL for another lanes value.
+ */
+int pjds_batch_create_lanes(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                            const int32_t *lanes, void *plan_dev, size_t plan_bytes, pjds_batch **out,
+                            void *stream);
+
+/*
+ * pjds_batch_create with another block-length rule: a tile whose rows'
+ * block holds at least min_len[2] entries gets 8 lanes per row, else 4 from
+ * min_len[1], else 2 from min_len[0], else one thread per row (tiles of
+ * 256 / lanes rows). The built-in rule is {2^31-1, 2^31-1, 64}. Errors as
+ * pjds_batch_create, and PJDS_EINVAL for a threshold below 1.
+ */
+int pjds_batch_create_rule(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                           const int32_t *min_len, void *plan_dev, size_t plan_bytes, pjds_batch **out,
+                           void *stream);
+
+/*
+ * Exhaustive autotuner of the batch's tiles (the f2 sweep applied to the
+ * whole persistent launch): for each of n_rules rules (rules[3 r .. 3 r + 2],
+ * as min_len above) builds the plan in plan_dev, runs it once, then times
+ * `reps` runs with CUDA events on `stream` (flush, if not NULL, is
+ * overwritten with cudaMemsetAsync before each timed run to empty L2) and
+ * writes the median microseconds to us[r]; *best receives the fastest rule.
+ * The vectors ys are overwritten. Errors as pjds_batch_create; PJDS_EINVAL
+ * for reps outside [1, 1000].
+ */
+int pjds_batch_tune_rule(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                         const int32_t *rules, int32_t n_rules, int32_t reps, void *plan_dev, size_t plan_bytes,
+                         void *flush, size_t flush_bytes, double *us, int32_t *best, void *stream);
+
+/*
  * Run the plan: reset the work counter and launch one persistent kernel
  * (one CTA per SM slot) whose CTAs take tiles from the counter until none is
  * left. use_graph = 1 records the two steps once into a CUDA graph kept in

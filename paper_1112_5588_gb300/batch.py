@@ -15,6 +15,12 @@ for _name, _res, _args in (
         ("pjds_spmm", ctypes.c_int, [_P(_p._PjdsDevS), _i32, _vp, _vp, _vp]),
         ("pjds_batch_plan_bytes", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_sz)]),
         ("pjds_batch_create", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_vp), _P(_vp), _vp, _sz, _P(_vp), _vp]),
+        ("pjds_batch_create_lanes", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_vp), _P(_vp), _P(_i32), _vp, _sz,
+                                                   _P(_vp), _vp]),
+        ("pjds_batch_create_rule", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_vp), _P(_vp), _P(_i32), _vp, _sz,
+                                                  _P(_vp), _vp]),
+        ("pjds_batch_tune_rule", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_vp), _P(_vp), _P(_i32), _i32, _i32, _vp,
+                                                _sz, _vp, _sz, _P(ctypes.c_double), _P(_i32), _vp]),
         ("pjds_batch_run", ctypes.c_int, [_vp, _i32, _vp]),
         ("pjds_batch_info", ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
         ("pjds_batch_destroy", ctypes.c_int, [_vp])):
@@ -39,7 +45,11 @@ def spmm(A, X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
 class Batch:
     """y_m = A_m x_m for many matrices in one persistent launch (pjds_batch_*)."""
 
-    def __init__(self, mats, xs, ys, stream=None):
+    def __init__(self, mats, xs, ys, lanes=None, rule=None, stream=None):
+        """lanes: None (the block-length rule) or one of 0, 1, 2, 4, 8 per
+        matrix (0 = the rule). rule: None (the built-in rule) or (L2, L4, L8),
+        the block lengths from which tiles get 2, 4 and 8 lanes per row (e.g.
+        from tune_rule)."""
         n = len(mats)
         if not (n == len(xs) == len(ys)) or n == 0:
             raise ValueError("need equal, non-empty lists of matrices, x and y")
@@ -54,8 +64,23 @@ class Batch:
         xp = (_vp * n)(*[x.data_ptr() for x in xs])
         yp = (_vp * n)(*[y.data_ptr() for y in ys])
         h = _vp()
-        _p._check(_lib.pjds_batch_create(n, self._structs, xp, yp, self.plan.data_ptr(), self.plan.numel(),
-                                         ctypes.byref(h), _p._stream_ptr(stream)), "pjds_batch_create")
+        if rule is not None:
+            if lanes is not None:
+                raise ValueError("give lanes or rule, not both")
+            mr = (_i32 * 3)(*[int(v) for v in rule])
+            _p._check(_lib.pjds_batch_create_rule(n, self._structs, xp, yp, mr, self.plan.data_ptr(),
+                                                  self.plan.numel(), ctypes.byref(h), _p._stream_ptr(stream)),
+                      "pjds_batch_create_rule")
+        elif lanes is None:
+            _p._check(_lib.pjds_batch_create(n, self._structs, xp, yp, self.plan.data_ptr(), self.plan.numel(),
+                                             ctypes.byref(h), _p._stream_ptr(stream)), "pjds_batch_create")
+        else:
+            if len(lanes) != n:
+                raise ValueError("lanes needs one entry per matrix")
+            ln = (_i32 * n)(*[int(v) for v in lanes])
+            _p._check(_lib.pjds_batch_create_lanes(n, self._structs, xp, yp, ln, self.plan.data_ptr(),
+                                                   self.plan.numel(), ctypes.byref(h), _p._stream_ptr(stream)),
+                      "pjds_batch_create_lanes")
         self._h = h
 
     def run(self, use_graph: bool = True, stream=None):
@@ -76,3 +101,34 @@ class Batch:
             self.destroy()
         except Exception:
             pass
+
+
+NEVER = 2**31 - 1
+# candidate block-length rules (L2, L4, L8) of tune_rule; the first is the built-in one
+DEFAULT_RULES = [(NEVER, NEVER, 64), (NEVER, NEVER, 32), (NEVER, NEVER, 128), (NEVER, NEVER, 16),
+                 (NEVER, 32, 128), (NEVER, 16, 64), (NEVER, 64, 256), (16, 64, 256), (8, 32, 128), (4, 16, 64)]
+
+
+def tune_rule(mats, xs, ys, rules=None, reps: int = 5, flush_bytes: int = 256 << 20, stream=None):
+    """Time the batch under each block-length rule (pjds_batch_tune_rule);
+    returns (best rule, [(rule, median us), ...]). Overwrites ys."""
+    rules = list(rules) if rules is not None else DEFAULT_RULES
+    n = len(mats)
+    for A, x, y in zip(mats, xs, ys):
+        _p._check_vec(x, A.n_cols, A.vec_dtype, "x")
+        _p._check_vec(y, A.n_rows, A.vec_dtype, "y")
+    structs = (_p._PjdsDevS * n)(*[A.struct for A in mats])
+    need = _sz()
+    _p._check(_lib.pjds_batch_plan_bytes(n, structs, ctypes.byref(need)), "pjds_batch_plan_bytes")
+    plan = torch.empty(max(need.value, 1), dtype=torch.uint8, device=xs[0].device)
+    flush = torch.empty(max(flush_bytes, 1), dtype=torch.uint8, device=xs[0].device) if flush_bytes else None
+    xp = (_vp * n)(*[x.data_ptr() for x in xs])
+    yp = (_vp * n)(*[y.data_ptr() for y in ys])
+    rr = (_i32 * (3 * len(rules)))(*[int(v) for r in rules for v in r])
+    us = (ctypes.c_double * len(rules))()
+    best = _i32()
+    _p._check(_lib.pjds_batch_tune_rule(n, structs, xp, yp, rr, len(rules), reps, plan.data_ptr(), plan.numel(),
+                                        flush.data_ptr() if flush is not None else None,
+                                        flush_bytes if flush is not None else 0, us, ctypes.byref(best),
+                                        _p._stream_ptr(stream)), "pjds_batch_tune_rule")
+    return tuple(rules[best.value]), [(tuple(r), float(u)) for r, u in zip(rules, us)]

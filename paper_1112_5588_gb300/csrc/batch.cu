@@ -182,13 +182,25 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d
   return acc;
 }
 
+// A tile of BT / LANES rows with LANES lanes each; the whole CTA stays for the
+// shuffles.
+template <typename TV, typename TX, int LANES>
+__device__ __forceinline__ void lanes_tile(const Desc &d, const int4 &tl, TX *y) {
+  const int32_t r = threadIdx.x / LANES, s = threadIdx.x % LANES;
+  const int64_t i = (int64_t)tl.y + r;
+  const bool active = r < tl.z && i < d.n_rows;
+  const auto acc = d.idx64 ? desc_row_lanes<TV, TX, int64_t, LANES>(d, i, s, active)
+                           : desc_row_lanes<TV, TX, int32_t, LANES>(d, i, s, active);
+  if (active && s == 0) y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
+}
+
 constexpr int LONG_LANES = 8;     // lanes per row in tiles of long rows
 constexpr int LONG_ROWS = BT / LONG_LANES;
 constexpr int LONG_MIN_LEN = 64;  // block length from which rows get LONG_LANES lanes
 
 // CTAs take tiles (matrix, first sorted row, rows, lanes per row) from a work
-// counter until none is left: short-row tiles have one row per thread,
-// long-row tiles LONG_ROWS rows with LONG_LANES lanes each. No CTA ever waits
+// counter until none is left: tiles of one lane per row have one row per
+// thread, tiles of 2, 4 or 8 lanes per row BT / lanes rows. No CTA ever waits
 // for another.
 template <typename TV, typename TX>
 __global__ void __launch_bounds__(BT)
@@ -210,13 +222,12 @@ __global__ void __launch_bounds__(BT)
         const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
         y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
       }
-    } else {  // the whole CTA stays for the shuffles
-      const int32_t r = threadIdx.x / LONG_LANES, s = threadIdx.x % LONG_LANES;
-      const int64_t i = (int64_t)tl.y + r;
-      const bool active = r < tl.z && i < d.n_rows;
-      const auto acc = d.idx64 ? desc_row_lanes<TV, TX, int64_t, LONG_LANES>(d, i, s, active)
-                               : desc_row_lanes<TV, TX, int32_t, LONG_LANES>(d, i, s, active);
-      if (active && s == 0) y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
+    } else if (tl.w == 2) {
+      lanes_tile<TV, TX, 2>(d, tl, y);
+    } else if (tl.w == 4) {
+      lanes_tile<TV, TX, 4>(d, tl, y);
+    } else {
+      lanes_tile<TV, TX, 8>(d, tl, y);
     }
   }
 }
@@ -331,10 +342,18 @@ extern "C" int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_
   return PJDS_OK;
 }
 
-extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
-                                 void *plan_dev, size_t plan_bytes, pjds_batch **out, void *stream) {
-  clear_error();
+// Plan: per matrix either fixed lanes (lanes[m] > 0) or the block-length
+// rule min_len (2, 4 or 8 lanes from block lengths min_len[0], [1], [2]).
+static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                      const int32_t *lanes, const int32_t *min_len, void *plan_dev, size_t plan_bytes,
+                      pjds_batch **out, void *stream) {
   if (n_mats <= 0 || !mats || !xs || !ys || !plan_dev || !out) return set_error(PJDS_EINVAL, "bad arguments");
+  if (lanes)
+    for (int32_t m = 0; m < n_mats; ++m)
+      if (lanes[m] != 0 && lanes[m] != 1 && lanes[m] != 2 && lanes[m] != 4 && lanes[m] != 8)
+        return set_error(PJDS_EINVAL, "lanes[%d] = %d: use 0, 1, 2, 4 or 8", m, lanes[m]);
+  for (int k = 0; k < 3; ++k)
+    if (min_len[k] < 1) return set_error(PJDS_EINVAL, "min_len[%d] = %d must be positive", k, min_len[k]);
   *out = nullptr;
   size_t need = 0;
   int rc = pjds_batch_plan_bytes(n_mats, mats, &need);
@@ -376,11 +395,13 @@ extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const voi
     cudaError_t e = cudaMemcpyAsync(bl.data(), A.block_len, sizeof(int32_t) * bl.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(PJDS_ECUDA, "read block lengths: %s", cudaGetErrorString(e));
-    // long-row tiles first (blocks are sorted by length), then short-row tiles
+    // long-row tiles first (blocks are sorted by length), then short-row
+    // tiles; or every tile with the matrix's given lanes per row
+    const int32_t fixed = lanes ? lanes[m] : 0;
     for (int64_t t0 = 0; t0 < A.n_rows;) {
       const int64_t L = bl[(size_t)(t0 / A.b)];
-      const bool lng = L >= LONG_MIN_LEN;
-      const int64_t rows = std::min<int64_t>(lng ? LONG_ROWS : BT, A.n_rows - t0);
+      const int32_t ln = fixed ? fixed : L >= min_len[2] ? 8 : L >= min_len[1] ? 4 : L >= min_len[0] ? 2 : 1;
+      const int64_t rows = std::min<int64_t>(BT / ln, A.n_rows - t0);
       // work estimate: stored entries of the tile's rows over the lanes per row
       int64_t cost = 0;
       for (int64_t r = t0; r < t0 + rows;) {
@@ -388,7 +409,7 @@ extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const voi
         cost += (end - r) * (int64_t)bl[(size_t)blk];
         r = end;
       }
-      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, lng ? LONG_LANES : 1, lng ? cost / LONG_LANES : cost});
+      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, ln, cost / ln});
       t0 += rows;
     }
   }
@@ -436,6 +457,30 @@ extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const voi
   h->exec = nullptr;
   *out = h;
   return PJDS_OK;
+}
+
+// the built-in rule: 8 lanes per row from block length 64, else one
+static const int32_t k_default_rule[3] = {0x7fffffff, 0x7fffffff, LONG_MIN_LEN};
+
+extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                                 void *plan_dev, size_t plan_bytes, pjds_batch **out, void *stream) {
+  clear_error();
+  return batch_plan(n_mats, mats, xs, ys, nullptr, k_default_rule, plan_dev, plan_bytes, out, stream);
+}
+
+extern "C" int pjds_batch_create_lanes(int32_t n_mats, const pjds_dev *mats, const void *const *xs,
+                                       void *const *ys, const int32_t *lanes, void *plan_dev, size_t plan_bytes,
+                                       pjds_batch **out, void *stream) {
+  clear_error();
+  return batch_plan(n_mats, mats, xs, ys, lanes, k_default_rule, plan_dev, plan_bytes, out, stream);
+}
+
+extern "C" int pjds_batch_create_rule(int32_t n_mats, const pjds_dev *mats, const void *const *xs,
+                                      void *const *ys, const int32_t *min_len, void *plan_dev, size_t plan_bytes,
+                                      pjds_batch **out, void *stream) {
+  clear_error();
+  if (!min_len) return set_error(PJDS_EINVAL, "min_len is NULL");
+  return batch_plan(n_mats, mats, xs, ys, nullptr, min_len, plan_dev, plan_bytes, out, stream);
 }
 
 static int batch_issue(pjds_batch *h, cudaStream_t s) {
@@ -495,4 +540,47 @@ extern "C" int pjds_batch_destroy(pjds_batch *h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   free(h);
   return PJDS_OK;
+}
+
+extern "C" int pjds_batch_tune_rule(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
+                                    const int32_t *rules, int32_t n_rules, int32_t reps, void *plan_dev,
+                                    size_t plan_bytes, void *flush, size_t flush_bytes, double *us, int32_t *best,
+                                    void *stream) {
+  clear_error();
+  if (!rules || n_rules <= 0 || !us || !best) return set_error(PJDS_EINVAL, "bad arguments");
+  if (reps < 1 || reps > 1000) return set_error(PJDS_EINVAL, "reps must be in [1, 1000]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) {
+    if (ev0) cudaEventDestroy(ev0);
+    return set_error(PJDS_ECUDA, "cudaEventCreate failed");
+  }
+  *best = -1;
+  int rc = PJDS_OK;
+  for (int32_t r = 0; r < n_rules && rc == PJDS_OK; ++r) {
+    us[r] = -1.0;
+    pjds_batch *h = nullptr;
+    rc = batch_plan(n_mats, mats, xs, ys, nullptr, rules + 3 * r, plan_dev, plan_bytes, &h, stream);
+    if (rc) break;
+    std::vector<float> t((size_t)reps);
+    rc = batch_issue(h, s);  // warm-up
+    for (int32_t k = 0; k < reps && rc == PJDS_OK; ++k) {
+      if (flush && flush_bytes) cudaMemsetAsync(flush, k & 0xff, flush_bytes, s);
+      cudaEventRecord(ev0, s);
+      rc = batch_issue(h, s);
+      cudaEventRecord(ev1, s);
+      const cudaError_t e = cudaEventSynchronize(ev1);
+      if (e != cudaSuccess && rc == PJDS_OK) rc = set_error(PJDS_ECUDA, "timing: %s", cudaGetErrorString(e));
+      if (rc == PJDS_OK) cudaEventElapsedTime(&t[(size_t)k], ev0, ev1);
+    }
+    pjds_batch_destroy(h);
+    if (rc) break;
+    std::sort(t.begin(), t.end());
+    const float med = reps % 2 ? t[(size_t)reps / 2] : 0.5f * (t[(size_t)reps / 2 - 1] + t[(size_t)reps / 2]);
+    us[r] = 1e3 * (double)med;
+    if (*best < 0 || us[r] < us[*best]) *best = r;
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  return rc;
 }

@@ -323,3 +323,32 @@ def test_host_stream_argument_checks_without_gpu(P):
     assert lib.pjds_spmv_host_stream(ref(s), 1, xh, yh, (V * 2)(None, 2048), yd, None) == -1
     assert lib.pjds_spmv_host_stream(ref(s), 1, xh, yh, (V * 2)(8, 8), yd, None) == -1
     assert b"distinct" in lib.pjds_last_error()
+
+
+def test_batch_lanes_checked_before_any_cuda_call(P):
+    from paper_1112_5588_gb300 import batch as Bt
+    A = tiny.random_lengths(64, 64, max_len=8, seed=1)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    s = (P._PjdsDevS * 1)(P._dev_struct_from_host(H))
+    V, I = ctypes.c_void_p, ctypes.c_int32
+    h = V()
+    for bad in (3, 16, -1):
+        rc = Bt._lib.pjds_batch_create_lanes(1, s, (V * 1)(4096), (V * 1)(8192), (I * 1)(bad), V(1 << 20), 1 << 20,
+                                             ctypes.byref(h), None)
+        assert rc == -1 and b"lanes" in P.lib().pjds_last_error()
+
+
+def test_batch_rule_checked_before_any_cuda_call(P):
+    from paper_1112_5588_gb300 import batch as Bt
+    A = tiny.random_lengths(64, 64, max_len=8, seed=1)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    s = (P._PjdsDevS * 1)(P._dev_struct_from_host(H))
+    V, I = ctypes.c_void_p, ctypes.c_int32
+    h = V()
+    rc = Bt._lib.pjds_batch_create_rule(1, s, (V * 1)(4096), (V * 1)(8192), (I * 3)(4, 0, 64), V(1 << 20), 1 << 20,
+                                        ctypes.byref(h), None)
+    assert rc == -1 and b"min_len" in P.lib().pjds_last_error()
+    us, best = (ctypes.c_double * 1)(), I()
+    rc = Bt._lib.pjds_batch_tune_rule(1, s, (V * 1)(4096), (V * 1)(8192), (I * 3)(4, 16, 64), 1, 0, V(1 << 20),
+                                      1 << 20, None, 0, us, ctypes.byref(best), None)
+    assert rc == -1 and b"reps" in P.lib().pjds_last_error()

@@ -177,3 +177,77 @@ def test_spmm_two_chunk_lanes(mods, oracle_lib, dtype, k):
         pjds.pjds_spmv_cfg(D, Xt[:, c].contiguous(), y1, threads_per_row=1, rows_per_thread=1, tile_order=-1)
         torch.cuda.synchronize()
         assert torch.equal(y1, Yt[:, c].contiguous()), c
+
+
+def test_batch_given_lanes(mods, oracle_lib):
+    # lanes per row given per matrix (as an autotuner would): every row equals
+    # the oracle, and bit for bit pjds_spmv_cfg with threads_per_row = lanes
+    torch, pjds, batch = mods
+    makes = [lambda: synth.zipf_rows(30_000, s=2.0, len_max=300, seed=31),
+             lambda: synth.hmep_like(n=40_000, seed=32),
+             lambda: tiny.random_lengths(1037, 1037, max_len=90, seed=33, p_empty=0.2),
+             lambda: synth.zipf_rows(12_000, s=1.6, len_max=512, seed=34),
+             lambda: synth.banded_uniform(n=20_000, seed=35),
+             lambda: tiny.random_lengths(333, 500, max_len=40, seed=36)]
+    lanes = [1, 2, 4, 8, 0, 2]
+    mats, devs, xs, ys = [], [], [], []
+    for k, make in enumerate(makes):
+        A = make()
+        D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32).to_device("cuda")
+        mats.append(A)
+        devs.append(D)
+        xs.append(torch.from_numpy(synth.vector(A.n_cols, seed=k)).cuda())
+        ys.append(torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda"))
+    B = batch.Batch(devs, xs, ys, lanes=lanes)
+    B.run(use_graph=True)
+    torch.cuda.synchronize()
+    for A, D, x, y, ln in zip(mats, devs, xs, ys, lanes):
+        xh = x.cpu().numpy()
+        r = parity.check_fp64(y.cpu().numpy(), oracle_lib.crs_spmv(A, xh), oracle_lib.crs_absmv(A, xh),
+                              np.diff(A.row_ptr))
+        assert r["ok"], (ln, r)
+        if ln:
+            y1 = torch.empty_like(y)
+            pjds.pjds_spmv_cfg(D, x, y1, threads_per_row=ln, unroll=4, tile_order=-1)
+            torch.cuda.synchronize()
+            assert torch.equal(y1, y), ln
+    B.destroy()
+    with pytest.raises(pjds.PjdsError):
+        batch.Batch(devs, xs, ys, lanes=[1, 2, 3, 8, 0, 2])
+
+
+def test_batch_rule_and_rule_tuner(mods, oracle_lib):
+    # tiles by a block-length rule: every rule gives oracle-exact rows; the
+    # built-in rule given explicitly is bit for bit the default plan; the
+    # tuner times each rule and picks the fastest
+    torch, pjds, batch = mods
+    mats, devs, xs, ys = [], [], [], []
+    for k in range(10):
+        A = synth.zipf_rows(int(5_000 + 7_000 * k), s=1.8 + 0.05 * k, len_max=400, seed=60 + k)
+        devs.append(pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32).to_device("cuda"))
+        xs.append(torch.from_numpy(synth.vector(A.n_cols, seed=k)).cuda())
+        ys.append(torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda"))
+        mats.append(A)
+    B0 = batch.Batch(devs, xs, ys)
+    B0.run(use_graph=False)
+    torch.cuda.synchronize()
+    y_default = [y.clone() for y in ys]
+    B0.destroy()
+    for rule in (batch.DEFAULT_RULES[0], (4, 16, 64), (2, 8, 32), (batch.NEVER, batch.NEVER, 1)):
+        for y in ys:
+            y.fill_(float("nan"))
+        B = batch.Batch(devs, xs, ys, rule=rule)
+        B.run(use_graph=True)
+        torch.cuda.synchronize()
+        for A, x, y in zip(mats, xs, ys):
+            xh = x.cpu().numpy()
+            r = parity.check_fp64(y.cpu().numpy(), oracle_lib.crs_spmv(A, xh), oracle_lib.crs_absmv(A, xh),
+                                  np.diff(A.row_ptr))
+            assert r["ok"], (rule, r)
+        if rule == batch.DEFAULT_RULES[0]:
+            assert all(torch.equal(a, b) for a, b in zip(y_default, ys))
+        B.destroy()
+    rules = batch.DEFAULT_RULES[:4]
+    best, timings = batch.tune_rule(devs, xs, ys, rules=rules, reps=3, flush_bytes=0)
+    assert len(timings) == 4 and all(us > 0 for _, us in timings)
+    assert best == min(timings, key=lambda t: t[1])[0]
