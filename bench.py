@@ -279,6 +279,7 @@ def run_ours(args, world, rank, local_rank):
         prec_gpu = precision_gpu_leg(torch, pjds, args, dev, flush)
         side["side"]["batching"] = batching_leg(torch, pjds, args, dev, flush)
         side["side"]["small_case"] = small_case_leg(torch, pjds, args, dev, flush)
+        side["side"]["tuning"] = tuning_leg(torch, pjds, args, dev)
 
     # ---------------- end to end through the C ABI from pinned host memory: K
     # products in one pjds_spmv_host_stream call (each step copies its x in
@@ -694,6 +695,33 @@ def batching_leg(torch, pjds, args, dev, flush):
     del devs, xs, ys
     torch.cuda.empty_cache()
     return out
+
+
+def tuning_leg(torch, pjds, args, dev):
+    """The threads-per-row / b sweep on the DLR-like matrix (long rows, fp32):
+    the exhaustive autotuner's 16 candidates (b in 32..256, T in 1..8) with
+    the L2 flushed between runs, against the paper's mapping (b = 32, one
+    thread per row), the library's default and the learned tuner's pick."""
+    import synth
+    from paper_1112_5588_gb300 import learned, tune
+    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=args.seed)
+    cands = tune.default_space(("f32",))
+    entries, best = tune.sweep(A, cands, reps=5)
+    us = {f"b{e['b']}_T{e['threads_per_row']}": round(e["us"], 2) for e in entries if e["status"] == 0}
+    paper = us["b32_T1"]
+    pick = learned.choose(A, cands)[1]
+    t_pick = us[f"b{pick['b']}_T{pick['threads_per_row']}"]
+    D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f32").to_device(dev)
+    x = torch.rand(A.n_cols, device=dev)
+    y = torch.empty(A.n_rows, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    t_def = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 10, 3, flush)) * 1e6
+    best_key = f"b{entries[best]['b']}_T{entries[best]['threads_per_row']}"
+    return {"matrix": f"DLR-like N={A.n_rows} nnz={A.nnz} (144/row), fp32", "sweep_us": us,
+            "best": best_key, "best_us": us[best_key], "paper_mapping_us": paper,
+            "default_mapping": pjds.pjds_spmv_resolve(D), "default_us": round(t_def, 2),
+            "learned_pick": f"b{pick['b']}_T{pick['threads_per_row']}", "learned_pick_us": t_pick,
+            "best_speedup_over_paper_mapping": round(paper / us[best_key], 3)}
 
 
 def precision_oracle_checks(oracle, pg):
