@@ -10,7 +10,9 @@ Matrices: hmep (--n rows), stencil (--g grid), dlr (--n rows, 144/row), zipf
 cg (one mixed-precision CG solve of `--reps` inner steps in the permuted
 basis, fp64 outer matrix, --dtype inner matrix, no graph) and lanczos
 (`--reps` steps, no graph) on the stencil; batch (--mats Zipf matrices with
-N log-uniform in [10k, --n], one persistent launch per repetition).
+N log-uniform in [10k, --n], one persistent launch per repetition); mlp (the
+learned tuner's cost model trained for `--reps` epochs on the committed
+timing data, then inference over the candidates of the held-out matrices).
 """
 from __future__ import annotations
 
@@ -27,7 +29,7 @@ def main(argv=None) -> int:
     ap.add_argument("--n", type=int, default=2_000_000)
     ap.add_argument("--g", type=int, default=100)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
-    ap.add_argument("--kind", choices=["spmv", "ellr", "spmm", "cg", "lanczos", "batch"], default="spmv")
+    ap.add_argument("--kind", choices=["spmv", "ellr", "spmm", "cg", "lanczos", "batch", "mlp"], default="spmv")
     ap.add_argument("--mats", type=int, default=64)
     ap.add_argument("--k", type=int, default=8)
     ap.add_argument("--permuted", action="store_true")
@@ -45,6 +47,8 @@ def main(argv=None) -> int:
     from . import batch, krylov, pjds
 
     dev = torch.device("cuda")
+    if a.kind == "mlp":
+        return run_mlp(a, torch)
     if a.kind == "batch":
         return run_batch(a, torch, synth, batch, pjds, dev)
     if a.kind in ("cg", "lanczos"):
@@ -106,6 +110,32 @@ def _timed(torch, run, reps, warmup):
         torch.cuda.synchronize()
         times.append(round(e0.elapsed_time(e1) * 1e3, 2))
     return times
+
+
+def run_mlp(a, torch) -> int:
+    import os
+    import time
+    from . import learned, tuner_data
+    data = dict(np.load(os.path.join(os.path.dirname(__file__), "data", "tuner_timings_gb300.npz"),
+                        allow_pickle=False))
+    X, y = tuner_data.samples(data, range(int(data["n_train"])))
+    m = learned.init(1)
+    learned.fit_scaling(m, X, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = learned.train(m, X, y, epochs=a.reps, batch=1024, lr=2e-3, seed=1)
+    t_train = time.perf_counter() - t0
+    cands = __import__("json").loads(str(data["cands"]))
+    rows = range(int(data["n_train"]), len(data["times_us"]))
+    enc = np.concatenate([learned.encode(data["features"][i], cands) for i in rows])
+    learned.predict(m, enc)
+    t0 = time.perf_counter()
+    learned.predict(m, enc)
+    t_pred = time.perf_counter() - t0
+    print(json.dumps({"kind": "mlp", "samples": int(len(y)), "epochs": a.reps, "train_s": round(t_train, 3),
+                      "s_per_epoch": round(t_train / max(a.reps, 1), 4), "loss_first": float(hist[0]),
+                      "loss_last": float(hist[-1]), "predict_rows": int(len(enc)), "predict_us": round(t_pred * 1e6, 1)}))
+    return 0
 
 
 def run_batch(a, torch, synth, batch, pjds, dev) -> int:
