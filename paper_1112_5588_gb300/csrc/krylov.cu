@@ -153,6 +153,43 @@ __device__ __forceinline__ typename dev::Acc<TV>::T row_product(const TV *__rest
   return acc;
 }
 
+// Two adjacent sorted rows i, i+1 (i even, so both lie in one block): one
+// paired load of col and of val per jagged diagonal, then each row's product
+// exactly as row_product computes it.
+template <typename TV, typename TX, typename IDX>
+__device__ __forceinline__ void row_product2(const TV *__restrict__ val, const int32_t *__restrict__ col,
+                                             const int64_t *__restrict__ col_start, int32_t L, int64_t i,
+                                             const TX *__restrict__ x, typename dev::Acc<TV>::T (&acc)[2]) {
+  using TA = typename dev::Acc<TV>::T;
+  constexpr int U = 4;
+  acc[0] = acc[1] = TA(0);
+  for (int32_t j = 0; j < L; j += U) {
+    int32_t c[U][2];
+    TV v[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < L) {
+        const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i;
+        dev::ld_stream<2>(col + o, c[u]);
+        dev::ld_stream<2>(val + o, v[u]);
+      } else {
+        c[u][0] = c[u][1] = -1;
+        v[u][0] = v[u][1] = TV{};
+      }
+    }
+    TX xv[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) xv[u][r] = dev::gather(x, c[u][r]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+        acc[r] = c[u][r] >= 0 ? dev::fma_acc(dev::to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
+  }
+}
+
 // The reducing kernels below run a grid of at most as many CTAs as fit on the
 // GPU at once and stride over the vectors (element i is taken by thread
 // i mod KT of CTA (i / KT) mod gridDim.x); each thread accumulates its own
@@ -185,6 +222,34 @@ __global__ void __launch_bounds__(KT)
       contrib += (double)yi * (double)yi;
     }
     y[i] = yi;
+  }
+  const double s = block_sum(contrib);
+  finish(s, f);
+}
+
+// y = A x and the reduction of sum x_i y_i with two adjacent rows per thread
+// (row pair p: rows 2p, 2p+1; the second is a padding row when n_rows is odd)
+template <typename TV, typename TX, typename IDX>
+__global__ void __launch_bounds__(KT)
+    spmv_dot2_kernel(const void *__restrict__ val_, const int32_t *__restrict__ col,
+                     const int64_t *__restrict__ col_start, const int32_t *__restrict__ block_len,
+                     const TX *__restrict__ x, TX *__restrict__ y, const TX *__restrict__ bv, Fin f, int32_t n_rows,
+                     int32_t b) {
+  const TV *__restrict__ val = static_cast<const TV *>(val_);
+  const int64_t n_pairs = ((int64_t)n_rows + 1) / 2;
+  double contrib = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * KT + threadIdx.x; p < n_pairs; p += (int64_t)gridDim.x * KT) {
+    const int64_t i = 2 * p;
+    const int32_t L = __ldg(block_len + (int32_t)(i / b));
+    typename dev::Acc<TV>::T acc[2];
+    row_product2<TV, TX, IDX>(val, col, col_start, L, i, x, acc);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (i + r < n_rows) {
+        const TX yi = (TX)acc[r];
+        contrib += (double)x[i + r] * (double)yi;
+        y[i + r] = yi;
+      }
   }
   const double s = block_sum(contrib);
   finish(s, f);
@@ -510,8 +575,21 @@ template <>
 int make_dot<double, 1>(const pjds_dev *A, Dot<double, 1> *d) {
   return make_dot_typed<double, double, 1>(A, d);
 }
+// fp32 / bf16 values: two rows per thread when val and col allow the paired
+// loads (one 8- or 4-byte value load and one 8-byte column load per diagonal)
+template <typename TV>
+static int make_dot2(const pjds_dev *A, Dot<float, 0> *d) {
+  if (A->n_stored + A->n_pad < 0x7fffffffLL)
+    d->fn = spmv_dot2_kernel<TV, float, int32_t>;
+  else
+    d->fn = spmv_dot2_kernel<TV, float, int64_t>;
+  return red_grid(d->fn, (int32_t)(((int64_t)A->n_rows + 1) / 2), &d->grid);
+}
+
 template <>
 int make_dot<float, 0>(const pjds_dev *A, Dot<float, 0> *d) {
+  const bool pair = ((uintptr_t)A->val % (2 * value_bytes(A->dtype))) == 0 && ((uintptr_t)A->col % 8) == 0;
+  if (pair) return A->dtype == PJDS_BF16 ? make_dot2<dev::bf16_t>(A, d) : make_dot2<float>(A, d);
   return A->dtype == PJDS_BF16 ? make_dot_typed<dev::bf16_t, float, 0>(A, d) : make_dot_typed<float, float, 0>(A, d);
 }
 
