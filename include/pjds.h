@@ -203,8 +203,8 @@ typedef struct pjds_launch {
   int32_t staged;
   int32_t index64;  /* 1: 64-bit element offsets even when 32 bits suffice (they are
                        used automatically from 2^31 stored entries on) */
-  int32_t tile_order;
-  int32_t reserved;
+  int32_t tile_order; /* 0 automatic, 1 the traversal table, -1 sorted order */
+  int32_t reserved;   /* 0 */
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
@@ -214,7 +214,9 @@ int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *
  * pjds_spmv default), with every 0 field replaced by its default, written to
  * *out; nothing is launched and no device memory is touched. Fields left at 0
  * take defaults; rows_per_thread > 1 alone implies threads_per_row = 1 and
- * vice versa. Returns PJDS_EINVAL for a combination pjds_spmv_cfg rejects.
+ * vice versa. out->tile_order is 1 (the table is used) or -1 (sorted order);
+ * out->reserved is 0. Returns PJDS_EINVAL for a combination pjds_spmv_cfg
+ * rejects.
  */
 int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *out);
 
