@@ -42,17 +42,18 @@ typedef struct pjds_batch pjds_batch;
 /*
  * Device bytes of the plan for these matrices: a work counter, one
  * descriptor per matrix and room for one entry per tile (an upper bound:
- * tiles hold 256 sorted rows, or 32 rows whose block has 64 or more entries,
- * each such row then shared by 8 lanes).
+ * every tile holds at least 32 sorted rows).
  */
 int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes);
 
 /*
  * Build a plan for y_m = A_m x_m, m < n_mats. mats[m] are device views of
  * pJDS matrices of one dtype (original or permuted basis each); xs[m], ys[m]
- * their device vectors. Each matrix is cut into tiles of sorted rows: 32
- * rows with 8 lanes per row while the rows' block has 64 or more entries,
- * then 256 rows with one thread per row. The tiles are grouped by matrix,
+ * their device vectors. Each matrix is cut into tiles of sorted rows by the
+ * length of the rows' block: 8 lanes per row from 256 entries, 4 from 64, 2
+ * from 16 (tiles of 256 / lanes rows), else one thread for two adjacent rows
+ * (tiles of 512 rows; one row per thread, 256 rows, when val and col do not
+ * allow paired loads). The tiles are grouped by matrix,
  * the matrix with the most stored work per lane first, and inside a matrix
  * ordered by their stored work per lane, largest first, so that the CTAs
  * work on one or two matrices at a time (their x stays in L2: 18% faster
@@ -83,7 +84,8 @@ int pjds_batch_create_lanes(int32_t n_mats, const pjds_dev *mats, const void *co
  * pjds_batch_create with another block-length rule: a tile whose rows'
  * block holds at least min_len[2] entries gets 8 lanes per row, else 4 from
  * min_len[1], else 2 from min_len[0], else one thread per row (tiles of
- * 256 / lanes rows). The built-in rule is {2^31-1, 2^31-1, 64}. Errors as
+ * 256 / lanes rows, two rows per thread below min_len[0] as above). The
+ * built-in rule is {16, 64, 256}. Errors as
  * pjds_batch_create, and PJDS_EINVAL for a threshold below 1.
  */
 int pjds_batch_create_rule(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,

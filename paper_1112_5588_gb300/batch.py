@@ -105,8 +105,8 @@ class Batch:
 
 NEVER = 2**31 - 1
 # candidate block-length rules (L2, L4, L8) of tune_rule; the first is the built-in one
-DEFAULT_RULES = [(NEVER, NEVER, 64), (NEVER, NEVER, 32), (NEVER, NEVER, 128), (NEVER, NEVER, 16),
-                 (NEVER, 32, 128), (NEVER, 16, 64), (NEVER, 64, 256), (16, 64, 256), (8, 32, 128), (4, 16, 64)]
+DEFAULT_RULES = [(16, 64, 256), (NEVER, NEVER, 64), (NEVER, NEVER, 32), (NEVER, NEVER, 128), (NEVER, NEVER, 16),
+                 (NEVER, 32, 128), (NEVER, 16, 64), (NEVER, 64, 256), (8, 32, 128), (4, 16, 64), (32, 128, 512)]
 
 
 def tune_rule(mats, xs, ys, rules=None, reps: int = 5, flush_bytes: int = 256 << 20, stream=None):

@@ -147,6 +147,43 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int6
   return acc;
 }
 
+// Two adjacent sorted rows i, i+1 (i even: one block) with paired loads of
+// col and val per jagged diagonal; each row's arithmetic as in desc_row.
+template <typename TV, typename TX, typename IDX>
+__device__ __forceinline__ void desc_row2(const Desc &d, int64_t i, typename dev::Acc<TV>::T (&acc)[2]) {
+  using TA = typename dev::Acc<TV>::T;
+  constexpr int U = 4;
+  const TV *__restrict__ val = static_cast<const TV *>(d.val);
+  const TX *__restrict__ x = static_cast<const TX *>(d.x);
+  const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
+  acc[0] = acc[1] = TA(0);
+  for (int32_t j = 0; j < L; j += U) {
+    int32_t c[U][2];
+    TV v[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (j + u < L) {
+        const IDX o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
+        dev::ld_stream<2>(d.col + o, c[u]);
+        dev::ld_stream<2>(val + o, v[u]);
+      } else {
+        c[u][0] = c[u][1] = -1;
+        v[u][0] = v[u][1] = TV{};
+      }
+    }
+    TX xv[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) xv[u][r] = dev::gather(x, c[u][r]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+        acc[r] = c[u][r] >= 0 ? dev::fma_acc(dev::to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
+  }
+}
+
 // LANES consecutive lanes share sorted row i: lane s takes jagged diagonals
 // s, s + LANES, ...; the partial sums are added with shuffles (fixed tree).
 template <typename TV, typename TX, typename IDX, int LANES>
@@ -216,7 +253,19 @@ __global__ void __launch_bounds__(BT)
     const int4 tl = tiles[t];
     const Desc d = descs[tl.x];
     TX *y = static_cast<TX *>(d.y);
-    if (tl.w == 1) {
+    if (tl.w == 0) {  // two adjacent rows per thread
+      const int32_t k = 2 * (int32_t)threadIdx.x;
+      const int64_t i = (int64_t)tl.y + k;
+      if (k < tl.z && i < d.n_rows) {
+        typename dev::Acc<TV>::T acc[2];
+        if (d.idx64)
+          desc_row2<TV, TX, int64_t>(d, i, acc);
+        else
+          desc_row2<TV, TX, int32_t>(d, i, acc);
+        y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc[0];
+        if (k + 1 < tl.z && i + 1 < d.n_rows) y[d.scatter ? (int64_t)__ldcs(d.perm + i + 1) : i + 1] = (TX)acc[1];
+      }
+    } else if (tl.w == 1) {
       const int64_t i = (int64_t)tl.y + threadIdx.x;
       if ((int32_t)threadIdx.x < tl.z && i < d.n_rows) {
         const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
@@ -398,10 +447,24 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
     // long-row tiles first (blocks are sorted by length), then short-row
     // tiles; or every tile with the matrix's given lanes per row
     const int32_t fixed = lanes ? lanes[m] : 0;
+    // one-lane tiles of the rule take two adjacent rows per thread when val
+    // and col allow the paired loads
+    const bool pair = !fixed && ((uintptr_t)A.val % (2 * value_bytes(dt))) == 0 && ((uintptr_t)A.col % 8) == 0;
+    auto lanes_of = [&](int64_t L) -> int32_t {
+      return fixed ? fixed : L >= min_len[2] ? 8 : L >= min_len[1] ? 4 : L >= min_len[0] ? 2 : 1;
+    };
     for (int64_t t0 = 0; t0 < A.n_rows;) {
-      const int64_t L = bl[(size_t)(t0 / A.b)];
-      const int32_t ln = fixed ? fixed : L >= min_len[2] ? 8 : L >= min_len[1] ? 4 : L >= min_len[0] ? 2 : 1;
-      const int64_t rows = std::min<int64_t>(BT / ln, A.n_rows - t0);
+      const int32_t ln = lanes_of(bl[(size_t)(t0 / A.b)]);
+      const int32_t per_tile = ln == 1 && pair ? 2 * BT : BT / ln;
+      // a tile ends where its rows' blocks fall into another lane class, so
+      // every row gets the lanes of its own block's length
+      int64_t end = std::min<int64_t>(t0 + per_tile, A.n_rows);
+      for (int64_t blk = t0 / A.b + 1; blk * A.b < end; ++blk)
+        if (lanes_of(bl[(size_t)blk]) != ln) {
+          end = blk * A.b;
+          break;
+        }
+      const int64_t rows = end - t0;
       // work estimate: stored entries of the tile's rows over the lanes per row
       int64_t cost = 0;
       for (int64_t r = t0; r < t0 + rows;) {
@@ -409,7 +472,7 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
         cost += (end - r) * (int64_t)bl[(size_t)blk];
         r = end;
       }
-      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, ln, cost / ln});
+      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, ln == 1 && pair ? 0 : ln, cost / ln});
       t0 += rows;
     }
   }
@@ -459,8 +522,10 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
   return PJDS_OK;
 }
 
-// the built-in rule: 8 lanes per row from block length 64, else one
-static const int32_t k_default_rule[3] = {0x7fffffff, 0x7fffffff, LONG_MIN_LEN};
+// the built-in rule: 2 lanes per row from block length 16, 4 from 64, 8 from
+// 256 (the fastest of the tuner's candidate rules on 64 uneven Zipf
+// matrices: 253 us against 281 us for 8 lanes from 64 and one below)
+static const int32_t k_default_rule[3] = {16, 64, 256};
 
 extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
                                  void *plan_dev, size_t plan_bytes, pjds_batch **out, void *stream) {

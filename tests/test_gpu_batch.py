@@ -114,7 +114,8 @@ def test_batch_uneven_matrices(mods, oracle_lib, dtype, graph):
         xh.append(x)
     B = batch.Batch(devs, xs, ys)
     info = B.info()
-    assert sum((A.n_rows + 255) // 256 for A, _, _ in mats) <= info["n_tiles"] <= sum(
+    # one-lane tiles hold 512 rows (two per thread), 8-lane tiles 32
+    assert sum((A.n_rows + 511) // 512 for A, _, _ in mats) <= info["n_tiles"] <= sum(
         (A.n_rows + 31) // 32 for A, _, _ in mats)
     for _ in range(2):
         for y in ys:
@@ -131,21 +132,26 @@ def test_batch_uneven_matrices(mods, oracle_lib, dtype, graph):
             check = parity.check_fp64 if dtype == "f64" else parity.check_fp32
             r = check(got, oracle_lib.crs_spmv(Ar, x), oracle_lib.crs_absmv(Ar, x), np.diff(A.row_ptr))
             assert r["ok"], r
-    # bit for bit the single product: rows whose block has >= 64 entries with 8
-    # threads per row, the others with one thread per row
+    # bit for bit the single product with the built-in rule's lanes: rows whose
+    # block has >= 256 entries with 8 threads per row, >= 64 with 4, >= 16 with
+    # 2, the others with one thread per row
     for m in (2, 5):
         A, perm, permuted = mats[m]
         H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype, permute_cols=permuted)
-        long_sorted = H.block_len[np.arange(A.n_rows) // 32] >= 64
-        y1, y8 = torch.empty_like(ys[m]), torch.empty_like(ys[m])
-        pjds.pjds_spmv_cfg(devs[m], xs[m], y1, threads_per_row=1)
-        pjds.pjds_spmv_cfg(devs[m], xs[m], y8, threads_per_row=8, unroll=4)
-        torch.cuda.synchronize()
+        bl = H.block_len[np.arange(A.n_rows) // 32]
+        lanes = np.where(bl >= 256, 8, np.where(bl >= 64, 4, np.where(bl >= 16, 2, 1)))
         out_row = np.arange(A.n_rows) if permuted else H.perm  # output row of sorted row i
-        want = y1.cpu().numpy().copy()
-        want[out_row[long_sorted]] = y8.cpu().numpy()[out_row[long_sorted]]
-        assert np.array_equal(want, ys[m].cpu().numpy()), m
-        assert long_sorted.any() or m == 2
+        want = np.full(A.n_rows, np.nan)
+        for t in (1, 2, 4, 8):
+            yt = torch.empty_like(ys[m])
+            if t == 1:
+                pjds.pjds_spmv_cfg(devs[m], xs[m], yt, threads_per_row=1, tile_order=-1)
+            else:
+                pjds.pjds_spmv_cfg(devs[m], xs[m], yt, threads_per_row=t, unroll=4, tile_order=-1)
+            torch.cuda.synchronize()
+            want[out_row[lanes == t]] = yt.double().cpu().numpy()[out_row[lanes == t]]
+        assert np.array_equal(want, ys[m].double().cpu().numpy()), m
+        assert (lanes > 1).any() or m == 2
     B.destroy()
 
 
