@@ -231,9 +231,7 @@ __device__ __forceinline__ void lanes_tile(const Desc &d, const int4 &tl, TX *y)
   if (active && s == 0) y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
 }
 
-constexpr int LONG_LANES = 8;     // lanes per row in tiles of long rows
-constexpr int LONG_ROWS = BT / LONG_LANES;
-constexpr int LONG_MIN_LEN = 64;  // block length from which rows get LONG_LANES lanes
+constexpr int MIN_TILE_ROWS = BT / 8;  // the smallest tile: 8 lanes per row
 
 // CTAs take tiles (matrix, first sorted row, rows, lanes per row) from a work
 // counter until none is left: tiles of one lane per row have one row per
@@ -379,8 +377,9 @@ extern "C" int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, v
 
 // ----------------------------------------------------------------------------- batch
 
-// upper bound of a matrix's tiles (every tile a long-row tile)
-static int64_t tiles_of(const pjds_dev &A) { return ((int64_t)A.n_rows + LONG_ROWS - 1) / LONG_ROWS; }
+// upper bound of a matrix's tiles: every tile but the last one of a matrix
+// starts and ends on a multiple of MIN_TILE_ROWS
+static int64_t tiles_of(const pjds_dev &A) { return ((int64_t)A.n_rows + MIN_TILE_ROWS - 1) / MIN_TILE_ROWS; }
 
 extern "C" int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes) {
   clear_error();
@@ -487,6 +486,11 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
     }
     return a.cost > b.cost;
   });
+  int64_t bound = 0;
+  for (int32_t m = 0; m < n_mats; ++m) bound += tiles_of(mats[m]);
+  if ((int64_t)tiles.size() > bound)
+    return set_error(PJDS_EINVAL, "plan of %zu tiles exceeds the %lld the plan buffer holds", tiles.size(),
+                     (long long)bound);
   std::vector<int4> tl(tiles.size());
   for (size_t i = 0; i < tiles.size(); ++i) tl[i] = make_int4(tiles[i].m, tiles[i].row0, tiles[i].rows, tiles[i].lanes);
   char *p = static_cast<char *>(plan_dev);
