@@ -47,17 +47,26 @@ L2_FLUSH_BYTES = 256 << 20
 # the launch configuration is the recorded one.
 NCU_TRAFFIC = {
     # profiles/pjds_rows_kernel_hmep6.2M_f64.md: 1.192 GB read + 23.1 MB write per launch
-    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_215_416_576, "src": "c40c4fc59d3c4bbb",
+    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_215_416_576, "src": "a917c8a9adf01a59",
                                    "cfg": {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 256,
                                            "unroll": 4, "staged": 0, "index64": 0, "tile_order": 1}},
 }
 
 
+def code_hash(text: str) -> str:
+    """Hash of C++ source without its // comments and blank lines, so a
+    change to the comments alone keeps the hash."""
+    lines = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code.strip():
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1112_5588_gb300", "csrc", "spmv_kernels.cuh"), "rb") as fh:
-        h.update(fh.read())
-    return h.hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_1112_5588_gb300", "csrc", "spmv_kernels.cuh")) as fh:
+        return code_hash(fh.read())
 
 
 def hbm_peak():

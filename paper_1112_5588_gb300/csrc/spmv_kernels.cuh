@@ -11,9 +11,14 @@
 //   - the j-loop is unrolled so each thread issues U independent val/col
 //     loads, then U gathers, before the dependent fused multiply-adds;
 //   - the accumulator stays in a register and y is written once (scattered
-//     through perm[] in the original basis).
+//     through perm[] in the original basis);
+//   - optionally the 32-row tiles are taken in the traversal order of
+//     tile_order (by the original index of each tile's first row), so the
+//     rows in flight are neighbours in the original numbering: their x
+//     gathers share L2 sectors and their y stores fill whole sectors.
 // Pad entries carry column -1 and are skipped, so every row's sum runs over
-// exactly its own entries in CRS order, as in Listing 2.
+// exactly its own entries in CRS order, as in Listing 2 (with T threads per
+// row, each lane over every T-th entry, then a fixed shuffle tree).
 #pragma once
 
 #include <cuda_bf16.h>
