@@ -257,3 +257,31 @@ def test_batch_rule_and_rule_tuner(mods, oracle_lib):
     best, timings = batch.tune_rule(devs, xs, ys, rules=rules, reps=3, flush_bytes=0)
     assert len(timings) == 4 and all(us > 0 for _, us in timings)
     assert best == min(timings, key=lambda t: t[1])[0]
+
+
+def test_batch_degenerate_matrices(mods, oracle_lib):
+    # a matrix without rows, one whose rows are all empty, a one-row matrix
+    # and two ordinary ones in one launch, with each way of choosing lanes
+    torch, pjds, batch = mods
+    makes = [lambda: tiny.from_lengths([], 5), lambda: tiny.from_lengths([0] * 77, 9),
+             lambda: tiny.from_lengths([3], 4, seed=1), lambda: synth.zipf_rows(3_000, s=2.0, len_max=300, seed=71),
+             lambda: tiny.random_lengths(515, 600, max_len=70, seed=72, p_empty=0.3)]
+    mats, devs, xs = [], [], []
+    for k, make in enumerate(makes):
+        A = make()
+        mats.append(A)
+        devs.append(pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32).to_device("cuda"))
+        xs.append(torch.from_numpy(synth.vector(A.n_cols, seed=k)).cuda())
+    for kw in (dict(), dict(rule=(4, 16, 64)), dict(lanes=[1, 2, 4, 8, 0])):
+        ys = [torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda") for A in mats]
+        B = batch.Batch(devs, xs, ys, **kw)
+        B.run(use_graph=True)
+        torch.cuda.synchronize()
+        for A, x, y in zip(mats, xs, ys):
+            if A.n_rows == 0:
+                continue
+            xh = x.cpu().numpy()
+            r = parity.check_fp64(y.cpu().numpy(), oracle_lib.crs_spmv(A, xh), oracle_lib.crs_absmv(A, xh),
+                                  np.diff(A.row_ptr))
+            assert r["ok"], (kw, r)
+        B.destroy()

@@ -328,5 +328,8 @@ def test_host_stream_equals_single_products(P, dtype, permute):
         P.pjds_spmv(D, xh.cuda(), ref)
         torch.cuda.synchronize()
         assert torch.equal(ref.cpu(), yh), v
-    # nothing to do: returns at once
+    # one vector, and nothing to do
+    y1 = [torch.full((A.n_rows,), float("nan"), dtype=D.vec_dtype).pin_memory()]
+    P.pjds_spmv_host_stream(D, xs[:1], y1, xd, yd)
+    assert torch.equal(y1[0], ys[0])
     P.pjds_spmv_host_stream(D, [], [], xd, yd)
