@@ -168,3 +168,35 @@ def test_batch_64_uneven_full(P, oracle_lib):
                               np.diff(M.row_ptr))
         assert r["ok"], r
     B.destroy()
+
+
+def test_stencil_lanczos_f32_ritz_refined_full(P, oracle_lib, stencil):
+    # the 200-step Lanczos of the precision workload at full size: fp32 values
+    # and vectors, the extreme Ritz pair refined in fp64; the refined Rayleigh
+    # quotient and residual equal the oracle's recomputation from the returned
+    # vector, and the refined value agrees with a 200-step fp64 run
+    import torch
+    from paper_1112_5588_gb300 import krylov
+    A = stencil
+    H32 = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f32", permute_cols=True)
+    perm = H32.perm.copy()
+    D32 = H32.to_device("cuda")
+    H32.destroy()
+    D64 = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64",
+                        permute_cols=True).to_device("cuda")
+    v0 = synth.vector(A.n_rows, seed=1236)[perm]
+    thetas = {}
+    for D in (D32, D64):
+        alpha, beta, V = krylov.lanczos(D, torch.from_numpy(v0).to("cuda", D.vec_dtype), 200, keep_basis=True)
+        th, s = krylov.tridiag_extreme(alpha, beta)
+        yv, th_ref, resid = krylov.ritz_refine(D64, V, s)
+        y = np.empty(A.n_rows)
+        y[perm] = yv.cpu().numpy()
+        Ay = oracle_lib.crs_spmv(A, y)
+        rq = float(y @ Ay / (y @ y))
+        assert th_ref == pytest.approx(rq, rel=1e-13)
+        assert resid == pytest.approx(float(np.linalg.norm(Ay - rq * y) / np.linalg.norm(y) / abs(rq)), rel=1e-6)
+        thetas[D.dtype] = th_ref
+        del V
+        torch.cuda.empty_cache()
+    assert thetas[1] == pytest.approx(thetas[0], rel=1e-10)
