@@ -554,6 +554,27 @@ def precision_gpu_leg(torch, pjds, args, dev, flush):
             t = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xv, yv, **kw), 10, 3, flush))
             rep[f"spmv_{dt}{tag}"] = {"gbs": round(nb / t / 1e9, 1), "us": round(t * 1e6, 2),
                                       "frac_of_hbm": round(nb / t / 1e9 / hbm_peak()[0], 4)}
+    # pJDS in the original basis against ELLPACK-R on the same matrix (fp64)
+    Ho = pjds.pjds_create(S.n_rows, S.n_cols, S.row_ptr, S.col, S.val, b=32, dtype="f64")
+    Do = Ho.to_device(dev)
+    Ho.destroy()
+    Eo = pjds.ellr_create(S.n_rows, S.n_cols, S.row_ptr, S.col, S.val, dtype="f64")
+    ell_stored = Eo.n_stored
+    ED = Eo.to_device(dev)
+    Eo.destroy()
+    xo = torch.from_numpy(synth.vector(n, seed=args.seed)).to(dev)
+    yo, ye = torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float64, device=dev)
+    t_po = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv(Do, xo, yo), 10, 3, flush))
+    t_eo = statistics.median(time_launches(torch, lambda: pjds.ellr_spmv(ED, xo, ye), 10, 3, flush))
+    nb_o = alg_bytes(n, n, S.nnz, 8, 8)
+    nb_e = alg_bytes(n, n, S.nnz, 8, 8, scatter=False) + 4 * n
+    rep["original_basis_f64"] = {"pjds_gbs": round(nb_o / t_po / 1e9, 1), "pjds_us": round(t_po * 1e6, 2),
+                                 "ellr_gbs": round(nb_e / t_eo / 1e9, 1), "ellr_us": round(t_eo * 1e6, 2),
+                                 "pjds_vs_ellr_speed": round(t_eo / t_po, 3),
+                                 "pjds_data_reduction_vs_ellpack": round(1 - Do.n_stored / ell_stored, 4),
+                                 "bit_identical": bool(torch.equal(yo, ye)) if not pjds.pjds_spmv_resolve(Do)[
+                                     "threads_per_row"] > 1 else None}
+    del Do, ED, xo, yo, ye
     b = synth.vector(n, seed=args.seed + 1)
     bp = torch.from_numpy(b[perm]).to(dev)
     runs = {"cg_fp64": (None, 1, 300), "cg_f32_refined": ("f32", 6, 50), "cg_bf16_refined": ("bf16", 12, 25)}
