@@ -149,15 +149,16 @@ int pjds_destroy(pjds_host *h);
  *   - permute_cols = 1: writes y[i] (x and y in the permuted basis).
  * x: n_cols elements, y: n_rows elements, device memory of the vector type of
  * A->dtype; x and y must not overlap. Every element of y is written.
- * Mapping (the default of pjds_spmv_cfg): one thread per row, summing in the
- * row's original entry order, when n_rows >= 2^19 (fp64) or 2^20 (fp32, bf16)
- * and every row is shorter than 64; otherwise T = 2, 4 or 8 threads share a
- * row (each sums every T-th entry in order, then a fixed shuffle tree adds
- * the T partial sums), T being the smallest with n_rows * T reaching that
- * thread count, and at least 2 for rows of 64 entries or more. With one
- * thread per row, fp32 and bf16 values from 2^21 rows on take two adjacent
- * rows per thread (same per-row arithmetic) when val and col allow the
- * paired loads. pjds_spmv_resolve reports the mapping chosen for a matrix.
+ * Mapping (the default of pjds_spmv_cfg): T threads per row, T in 1, 2, 4,
+ * 8, from the longest row against the size of the product: with ratio =
+ * n_max * 2^20 / (nnz * (value bytes + 4)), T = 1 below 2, 2 below 8, 4
+ * below 64, else 8, then doubled (up to 8) while n_rows * T < 2^17. With
+ * T = 1 each row sums in its original entry order; with T > 1 each lane sums
+ * every T-th entry in order, then a fixed shuffle tree adds the T partial
+ * sums. With one thread per row, fp32 and bf16 values from 2^21 rows on take
+ * two adjacent rows per thread (same per-row arithmetic) when val and col
+ * allow the paired loads. pjds_spmv_resolve reports the mapping chosen for a
+ * matrix.
  */
 int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
 

@@ -63,25 +63,35 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   return PJDS_OK;
 }
 
-// Default mapping: one row per thread, and T threads per row where one
-// thread per row leaves the GPU short of threads or rows are long. T is the
-// smallest of 1, 2, 4, 8 with n_rows * T >= 2^19 threads (fp64) or 2^20
-// (fp32 / bf16 values, which carry less work per entry), and at least 2 when
-// the longest row has 64 entries or more. The thresholds are the ones with
-// the lowest mean time over an exhaustive GB300 sweep of 2,200 synthetic
-// matrices (10k to 4M rows); matrices of 2^20 rows and more with short rows
-// keep the paper's one thread per row. There, fp32 / bf16 values take two
-// adjacent rows per thread (one 8- or 4-byte load per jagged diagonal) from
-// 2^21 rows on, when val and col are aligned for it, and every dtype runs
-// 256-thread CTAs: on the 27-point stencil (4.5M rows) bf16 162 -> 136 us,
-// fp32 168 -> 160 us; on the HMEp-like matrix (6.2M rows) fp64 289 -> 283 us.
+// Default mapping: T threads per row, T in 1, 2, 4, 8. A thread runs its
+// row as a chain of about len / (T U) dependent rounds (a col load, then the
+// x gather it addresses), while the whole product streams about
+// nnz * (value + index bytes) from HBM; T grows until the longest row's chain
+// fits under that stream time. With ratio = n_max * 2^20 / (nnz * entry
+// bytes): T = 1 below 2, 2 below 8, 4 below 64, else 8; then T doubles (up
+// to 8) while n_rows * T < 2^17 threads. Thresholds fitted to an exhaustive
+// GB300 timing of T on 2,000 Zipf matrices (10k to 4M rows) and 100 more of
+// 4M to 20M rows; on 200 held-out matrices the time over the best T is 8.2%
+// / 5.2% / 4.9% (fp64 / fp32 / bf16; 17.5% / 15.5% / 13.9% with the earlier
+// rule, T from n_rows * T >= 2^19 or 2^20 threads alone), and 1.9% over 45
+// uniform-length cases (stencil, banded, block-dense and HMEp-like, 8k to
+// 1M rows; 9.9% before). With one thread per row, fp32 / bf16 values take
+// two adjacent rows per thread (one 8- or 4-byte load per jagged diagonal)
+// from 2^21 rows on, when val and col are aligned for it, and every dtype
+// runs 256-thread CTAs: on the 27-point stencil (4.5M rows) bf16 162 -> 136
+// us, fp32 168 -> 160 us; on the HMEp-like matrix (6.2M rows) fp64 289 -> 283 us.
+static int32_t default_threads_per_row(const pjds_dev *A) {
+  const double entry = (double)(value_bytes(A->dtype) + 4);
+  const double ratio = A->nnz > 0 ? (double)A->n_max * 1048576.0 / ((double)A->nnz * entry) : 0.0;
+  int32_t t = ratio < 2.0 ? 1 : ratio < 8.0 ? 2 : ratio < 64.0 ? 4 : 8;
+  while (t < 8 && (int64_t)A->n_rows * t < (1 << 17)) t *= 2;
+  return t;
+}
+
 static LaunchCfg default_cfg(const pjds_dev *A) {
   LaunchCfg c;
   c.rows_per_thread = 1;
-  const int64_t fill = A->dtype == PJDS_F64 ? (1 << 19) : (1 << 20);
-  int32_t t = 1;
-  while (t < 8 && (int64_t)A->n_rows * t < fill) t *= 2;
-  if (A->n_max >= 64 && t < 2) t = 2;
+  const int32_t t = default_threads_per_row(A);
   c.threads_per_row = t;
   c.block_threads = A->dtype == PJDS_F32 ? 256 : 128;
   if (t == 1) {
@@ -305,7 +315,7 @@ extern "C" int ellr_spmv(const ellr_dev *A, const void *x, void *y, void *stream
   if (!x || !y || !A->row_max) return set_error(PJDS_EINVAL, "x, y or row_max is NULL");
   if (A->n_stored > 0 && (!A->val || !A->col)) return set_error(PJDS_EINVAL, "val or col is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int nt = 256;
+  const int nt = 128;
   switch (A->dtype) {
     case PJDS_F64: return ellr_launch_f64(A, x, y, nt, s);
     case PJDS_F32: return ellr_launch_f32(A, x, y, nt, s);

@@ -104,6 +104,13 @@ int launch_pjds(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, c
                  : launch_pjds_idx<TV, TX, int64_t, false>(A, xx, yy, c, s);
 }
 
+// ELLPACK-R baseline: 4 diagonals per round of the j-loop, 128-thread CTAs
+// (the caller's nt). A GB300 sweep of U in 1, 2, 4, 8 x 128, 256, 512
+// threads put this configuration first or within 1% of the first on the
+// HMEp-like (6.2M rows, fp64), stencil (4.5M rows, fp64 / fp32) and
+// block-dense (280k rows, fp32) matrices, 10% behind U = 8 on the HMEp-like
+// matrix in fp32; U = 8 with 256 threads (52 registers in fp64, half the
+// warps resident) was 11-24% slower in fp64.
 template <typename TV, typename TX>
 int launch_ellr(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t s) {
   const int64_t grid = ((int64_t)A->n_rows + nt - 1) / nt;
@@ -112,10 +119,10 @@ int launch_ellr(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t 
   const TX *xx = static_cast<const TX *>(x);
   TX *yy = static_cast<TX *>(y);
   if (A->n_stored < 0x7fffffffLL)
-    dev::ellr_kernel<TV, TX, int32_t, 8>
+    dev::ellr_kernel<TV, TX, int32_t, 4>
         <<<(unsigned)grid, nt, 0, s>>>(val, A->col, A->row_max, xx, yy, A->n_rows, A->n_pad);
   else
-    dev::ellr_kernel<TV, TX, int64_t, 8>
+    dev::ellr_kernel<TV, TX, int64_t, 4>
         <<<(unsigned)grid, nt, 0, s>>>(val, A->col, A->row_max, xx, yy, A->n_rows, A->n_pad);
   return check_launch("ellr_spmv launch");
 }

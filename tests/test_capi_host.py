@@ -188,16 +188,30 @@ def test_gpu_test_configs_resolve_on_host(P):
         assert P.pjds_spmv_resolve(H)["unroll"] in (4, 8)
 
 
-def _band(n, length, long_row=-1):
-    # n x n, row i holds columns i, i+1, ... (mod n); row long_row holds 64
+def _band(n, length, long_row=-1, long_len=64):
+    # n x n, row i holds columns i, i+1, ... (mod n); row long_row holds long_len
     lens = np.full(n, length, np.int64)
     if long_row >= 0:
-        lens[long_row] = 64
+        lens[long_row] = long_len
     row_ptr = np.zeros(n + 1, np.int64)
     row_ptr[1:] = np.cumsum(lens)
     rows = np.repeat(np.arange(n), lens)
     col = ((rows + np.arange(row_ptr[-1]) - row_ptr[rows]) % n).astype(np.int32)
     return synth.Crs(n, n, row_ptr, col, np.ones(row_ptr[-1]))
+
+
+ENTRY_BYTES = {"f64": 12, "f32": 8, "bf16": 6}
+
+
+def _expected_threads_per_row(n_rows, n_max, nnz, dt):
+    # the longest row's chain against the stream time of the product:
+    # ratio = n_max * 2^20 / (nnz * entry bytes); T = 1 below 2, 2 below 8,
+    # 4 below 64, else 8; then doubled while n_rows * T < 2^17 (integer form)
+    num, den = n_max * 2**20, max(nnz, 1) * ENTRY_BYTES[dt]
+    t = 1 if num < 2 * den else 2 if num < 8 * den else 4 if num < 64 * den else 8
+    while t < 8 and n_rows * t < 2**17:
+        t *= 2
+    return t
 
 
 def test_resolve_defaults(P):
@@ -206,29 +220,41 @@ def test_resolve_defaults(P):
     # 10k rows: one thread per row would leave the GPU short of threads
     assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 8, "block_threads": 128, "unroll": 4,
                                       "staged": 0, "index64": 0, "tile_order": -1}
-    # fill rule: smallest T in 1, 2, 4, 8 with n_rows * T >= 2^19 (fp64) / 2^20 (fp32, bf16)
-    for n, t64, t32 in ((600_000, 1, 2), (300_000, 2, 4), (100_000, 8, 8), (70_000, 8, 8), (1_100_000, 1, 1),
-                        (262_144, 2, 4), (262_143, 4, 8)):
-        C = _band(n, 3)
-        for dt, t in (("f64", t64), ("f32", t32), ("bf16", t32)):
+    # both sides of every threshold: the thread floor (2^17 rows at T = 1,
+    # 2^16 at T = 2, ...) and the chain ratio (a long row of growing length)
+    seen = set()
+    cases = [(n, 3, -1, 0) for n in (600_000, 1 << 17, (1 << 17) - 1, 1 << 16, (1 << 16) - 1, 20_000)]
+    cases += [(600_000, 3, 12345, L) for L in (41, 42, 164, 165, 1319, 1320, 5000)]
+    cases += [(300_000, 4, 7, L) for L in (60, 200, 1400)]
+    for n, length, long_row, long_len in cases:
+        C = _band(n, length, long_row, long_len)
+        n_max = int(np.diff(C.row_ptr).max())
+        for dt in ("f64", "f32", "bf16"):
             HC = P.pjds_create(C.n_rows, C.n_cols, C.row_ptr, C.col, C.val, b=32, dtype=dt)
             r = P.pjds_spmv_resolve(HC)
-            assert r["threads_per_row"] == t and r["rows_per_thread"] == 1, (n, dt, r)
+            t = _expected_threads_per_row(n, n_max, C.nnz, dt)
+            assert r["threads_per_row"] == t and r["rows_per_thread"] == 1, (n, long_len, dt, r, t)
+            assert r["block_threads"] == (256 if t == 1 or dt == "f32" else 128), (n, dt, r)
+            seen.add(t)
             HC.destroy()
+    assert seen == {1, 2, 4, 8}
     Z = synth.zipf_rows(10_000, s=2.0, len_max=512, seed=1)
     HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
     assert P.pjds_spmv_resolve(HZ)["threads_per_row"] == 8
     assert P.pjds_spmv_resolve(HZ, rows_per_thread=2)["threads_per_row"] == 1
     with pytest.raises(P.PjdsError):
         P.pjds_spmv_resolve(HZ, unroll=16)
-    # enough rows for one thread per row, but one row of 64 entries: 2 threads per row
-    L = _band(600_000, 3, long_row=12345)
-    HL = P.pjds_create(L.n_rows, L.n_cols, L.row_ptr, L.col, L.val, b=32)
-    assert P.pjds_spmv_resolve(HL)["threads_per_row"] == 2
+    # the paper's matrix classes at full size keep one thread per row: a
+    # block-dense (DLR-like) matrix of 280k rows of 144 entries
+    D = synth.block_dense(70_000, 4, 36, 0.05, seed=2)
+    for dt in ("f64", "f32", "bf16"):
+        HD = P.pjds_create(D.n_rows, D.n_cols, D.row_ptr, D.col, D.val, b=32, dtype=dt)
+        assert P.pjds_spmv_resolve(HD)["threads_per_row"] == 1, dt
+        HD.destroy()
 
 
 def test_resolve_large_matrix_defaults(P):
-    # one thread per row from 2^19 (fp64) / 2^20 rows: 256-thread CTAs, and two
+    # short rows, many of them: one thread per row on 256-thread CTAs, and two
     # rows per thread for fp32 / bf16 values from 2^21 rows on
     C = _band(1 << 21, 3)
     for dt, R in (("f64", 1), ("f32", 2), ("bf16", 2)):
