@@ -52,8 +52,9 @@ int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes);
  * their device vectors. Each matrix is cut into tiles of sorted rows by the
  * length of the rows' block: 8 lanes per row from 256 entries, 4 from 64, 2
  * from 16 (tiles of 256 / lanes rows), else one thread for two adjacent rows
- * (tiles of 512 rows; one row per thread, 256 rows, when val and col do not
- * allow paired loads). The tiles are grouped by matrix,
+ * (tiles of 512 rows), or for four when the block has at most 2 entries and
+ * val and col are 16-byte aligned (tiles of 1024 rows); one row per thread,
+ * 256 rows, when val and col do not allow paired loads. The tiles are grouped by matrix,
  * the matrix with the most stored work per lane first, and inside a matrix
  * ordered by their stored work per lane, largest first, so that the CTAs
  * work on one or two matrices at a time (their x stays in L2: 18% faster

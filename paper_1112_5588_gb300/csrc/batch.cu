@@ -147,41 +147,62 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int6
   return acc;
 }
 
-// Two adjacent sorted rows i, i+1 (i even: one block) with paired loads of
-// col and val per jagged diagonal; each row's arithmetic as in desc_row.
-template <typename TV, typename TX, typename IDX>
-__device__ __forceinline__ void desc_row2(const Desc &d, int64_t i, typename dev::Acc<TV>::T (&acc)[2]) {
+// R adjacent sorted rows i .. i+R-1 (i a multiple of R: one block) with one
+// vector load of col and of val per jagged diagonal, U diagonals per round;
+// each row's arithmetic as in desc_row.
+template <typename TV, typename TX, typename IDX, int R, int U>
+__device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev::Acc<TV>::T (&acc)[R]) {
   using TA = typename dev::Acc<TV>::T;
-  constexpr int U = 4;
   const TV *__restrict__ val = static_cast<const TV *>(d.val);
   const TX *__restrict__ x = static_cast<const TX *>(d.x);
   const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
-  acc[0] = acc[1] = TA(0);
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = TA(0);
   for (int32_t j = 0; j < L; j += U) {
-    int32_t c[U][2];
-    TV v[U][2];
+    int32_t c[U][R];
+    TV v[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (j + u < L) {
         const IDX o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
-        dev::ld_stream<2>(d.col + o, c[u]);
-        dev::ld_stream<2>(val + o, v[u]);
+        dev::ld_stream<R>(d.col + o, c[u]);
+        dev::ld_stream<R>(val + o, v[u]);
       } else {
-        c[u][0] = c[u][1] = -1;
-        v[u][0] = v[u][1] = TV{};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          c[u][r] = -1;
+          v[u][r] = TV{};
+        }
       }
     }
-    TX xv[U][2];
+    TX xv[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < 2; ++r) xv[u][r] = dev::gather(x, c[u][r]);
+      for (int r = 0; r < R; ++r) xv[u][r] = dev::gather(x, c[u][r]);
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < R; ++r)
         acc[r] = c[u][r] >= 0 ? dev::fma_acc(dev::to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
   }
+}
+
+// R adjacent rows per thread from the tile's first row; rows past the tile
+// or the matrix are not stored.
+template <typename TV, typename TX, int R, int U>
+__device__ __forceinline__ void rows_tile(const Desc &d, const int4 &tl, TX *y) {
+  const int32_t k = R * (int32_t)threadIdx.x;
+  const int64_t i = (int64_t)tl.y + k;
+  if (k >= tl.z || i >= d.n_rows) return;
+  typename dev::Acc<TV>::T acc[R];
+  if (d.idx64)
+    desc_rows<TV, TX, int64_t, R, U>(d, i, acc);
+  else
+    desc_rows<TV, TX, int32_t, R, U>(d, i, acc);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (k + r < tl.z && i + r < d.n_rows) y[d.scatter ? (int64_t)__ldcs(d.perm + i + r) : i + r] = (TX)acc[r];
 }
 
 // LANES consecutive lanes share sorted row i: lane s takes jagged diagonals
@@ -238,8 +259,8 @@ constexpr int MIN_TILE_ROWS = BT / 8;  // the smallest tile: 8 lanes per row
 // thread, tiles of 2, 4 or 8 lanes per row BT / lanes rows. No CTA ever waits
 // for another.
 template <typename TV, typename TX>
-__global__ void __launch_bounds__(BT)
-    batch_kernel(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
+__device__ __forceinline__ void
+    batch_body(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
                  int32_t *__restrict__ counter) {
   __shared__ int32_t s_tile;
   for (;;) {
@@ -252,17 +273,9 @@ __global__ void __launch_bounds__(BT)
     const Desc d = descs[tl.x];
     TX *y = static_cast<TX *>(d.y);
     if (tl.w == 0) {  // two adjacent rows per thread
-      const int32_t k = 2 * (int32_t)threadIdx.x;
-      const int64_t i = (int64_t)tl.y + k;
-      if (k < tl.z && i < d.n_rows) {
-        typename dev::Acc<TV>::T acc[2];
-        if (d.idx64)
-          desc_row2<TV, TX, int64_t>(d, i, acc);
-        else
-          desc_row2<TV, TX, int32_t>(d, i, acc);
-        y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc[0];
-        if (k + 1 < tl.z && i + 1 < d.n_rows) y[d.scatter ? (int64_t)__ldcs(d.perm + i + 1) : i + 1] = (TX)acc[1];
-      }
+      rows_tile<TV, TX, 2, 4>(d, tl, y);
+    } else if (tl.w == 3) {  // four adjacent rows per thread (rows of at most k_quad_max_len entries)
+      rows_tile<TV, TX, 4, 1>(d, tl, y);
     } else if (tl.w == 1) {
       const int64_t i = (int64_t)tl.y + threadIdx.x;
       if ((int32_t)threadIdx.x < tl.z && i < d.n_rows) {
@@ -277,6 +290,23 @@ __global__ void __launch_bounds__(BT)
       lanes_tile<TV, TX, 8>(d, tl, y);
     }
   }
+}
+
+template <typename TV, typename TX>
+__global__ void __launch_bounds__(BT)
+    batch_kernel(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
+                 int32_t *__restrict__ counter) {
+  batch_body<TV, TX>(descs, tiles, n_tiles, counter);
+}
+
+// fp64 values: six resident CTAs per SM. Without the bound the four-row path
+// takes the kernel from 40 to 48 registers and five CTAs per SM (253 against
+// 237 us on the Zipf batch); fp32 and bf16 stay at 40 registers unbounded,
+// while the same bound made fp32 spill (222 against 214 us).
+__global__ void __launch_bounds__(BT, 6)
+    batch_kernel_f64(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
+                     int32_t *__restrict__ counter) {
+  batch_body<double, double>(descs, tiles, n_tiles, counter);
 }
 
 static inline size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -392,6 +422,13 @@ extern "C" int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_
 
 // Plan: per matrix either fixed lanes (lanes[m] > 0) or the block-length
 // rule min_len (2, 4 or 8 lanes from block lengths min_len[0], [1], [2]).
+// Longest block (entries per row) whose rows a tile of the rule takes four at
+// a time per thread: on 64 Zipf matrices (9.8M rows, 61% of them with one
+// entry) 253 -> 237 us in fp64, 241 -> 214 us in fp32, 214 -> 208 us in bf16
+// against two rows per thread, with the same bits (thresholds 1 and 4 within
+// 1%).
+constexpr int32_t k_quad_max_len = 2;
+
 static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
                       const int32_t *lanes, const int32_t *min_len, void *plan_dev, size_t plan_bytes,
                       pjds_batch **out, void *stream) {
@@ -449,17 +486,28 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
     // one-lane tiles of the rule take two adjacent rows per thread when val
     // and col allow the paired loads
     const bool pair = !fixed && ((uintptr_t)A.val % (2 * value_bytes(dt))) == 0 && ((uintptr_t)A.col % 8) == 0;
+    // and four adjacent rows per thread for blocks of at most k_quad_max_len
+    // entries when val and col allow 16-byte loads
+    const bool quad = pair && ((uintptr_t)A.val % 16) == 0 && ((uintptr_t)A.col % 16) == 0;
     auto lanes_of = [&](int64_t L) -> int32_t {
       return fixed ? fixed : L >= min_len[2] ? 8 : L >= min_len[1] ? 4 : L >= min_len[0] ? 2 : 1;
     };
+    // tile kind: 8, 4 or 2 lanes per row, 1 (one row per thread), 0 (two
+    // rows per thread) or 3 (four rows per thread)
+    auto kind_of = [&](int64_t L) -> int32_t {
+      const int32_t ln = lanes_of(L);
+      if (ln != 1 || !pair) return ln;
+      return quad && L <= k_quad_max_len ? 3 : 0;
+    };
     for (int64_t t0 = 0; t0 < A.n_rows;) {
-      const int32_t ln = lanes_of(bl[(size_t)(t0 / A.b)]);
-      const int32_t per_tile = ln == 1 && pair ? 2 * BT : BT / ln;
-      // a tile ends where its rows' blocks fall into another lane class, so
-      // every row gets the lanes of its own block's length
+      const int32_t kind = kind_of(bl[(size_t)(t0 / A.b)]);
+      const int32_t ln = kind == 0 || kind == 3 ? 1 : kind;
+      const int32_t per_tile = kind == 3 ? 4 * BT : kind == 0 ? 2 * BT : BT / ln;
+      // a tile ends where its rows' blocks fall into another kind, so every
+      // row gets the mapping of its own block's length
       int64_t end = std::min<int64_t>(t0 + per_tile, A.n_rows);
       for (int64_t blk = t0 / A.b + 1; blk * A.b < end; ++blk)
-        if (lanes_of(bl[(size_t)blk]) != ln) {
+        if (kind_of(bl[(size_t)blk]) != kind) {
           end = blk * A.b;
           break;
         }
@@ -471,7 +519,7 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
         cost += (end - r) * (int64_t)bl[(size_t)blk];
         r = end;
       }
-      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, ln == 1 && pair ? 0 : ln, cost / ln});
+      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, kind, cost / ln});
       t0 += rows;
     }
   }
@@ -506,7 +554,7 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (dt == PJDS_F64)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double, double>, BT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_f64, BT, 0);
   else if (dt == PJDS_F32)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float, float>, BT, 0);
   else
@@ -556,7 +604,7 @@ static int batch_issue(pjds_batch *h, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(h->counter, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return set_error(PJDS_ECUDA, "reset counter: %s", cudaGetErrorString(e));
   if (h->dtype == PJDS_F64)
-    batch_kernel<double, double><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
+    batch_kernel_f64<<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
   else if (h->dtype == PJDS_F32)
     batch_kernel<float, float><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
   else
