@@ -98,6 +98,8 @@ typedef struct pjds_host {
   int32_t *col;       /* [n_stored] */
   void *val;          /* [n_stored] of dtype */
   int32_t *tile_order; /* [n_pad / 32] */
+  int32_t *plan;       /* [4 * n_plan] per-tile mapping, see pjds_dev */
+  int32_t n_plan, plan_reserved;
 } pjds_host;
 
 /*
@@ -110,6 +112,17 @@ typedef struct pjds_host {
  * kernels follow it when pjds_launch.tile_order selects it (a kernel skips an
  * entry outside that range); the staged kernel, SpMM, the batched launch and
  * the Krylov products take tiles in sorted order.
+ * plan (n_plan entries of four int32: 0, first sorted row, rows, kind) is
+ * the per-tile mapping pjds_create wrote, or NULL: the sorted rows cut into
+ * tiles of one 256-thread CTA each, every tile mapped by the length of its
+ * rows' block: 8 lanes per row from 256 entries, 4 from 64, 2 from 16 (kinds
+ * 8, 4, 2; 256 / lanes rows), else two adjacent rows per thread (kind 0, 512
+ * rows) or four for blocks of at most 2 entries (kind 3, 1024 rows); a tile
+ * ends where the kind changes, and the entries are ordered by work per lane,
+ * largest first. A row gives the same bits as with the same lanes per row in
+ * the uniform mappings (one thread per row for kinds 0 and 3). The plan
+ * kernel runs one CTA per entry; it needs plan, val and col 16-byte aligned
+ * and skips an entry that does not describe a tile of the matrix.
  * val must be 16-byte aligned; all other pointers 4-byte aligned.
  */
 typedef struct pjds_dev {
@@ -123,6 +136,8 @@ typedef struct pjds_dev {
   const int32_t *col;
   const void *val;
   const int32_t *tile_order; /* NULL: tiles in sorted order */
+  const int32_t *plan;       /* NULL: no per-tile mapping */
+  int32_t n_plan, plan_reserved;
 } pjds_dev;
 
 /*
@@ -149,8 +164,11 @@ int pjds_destroy(pjds_host *h);
  *   - permute_cols = 1: writes y[i] (x and y in the permuted basis).
  * x: n_cols elements, y: n_rows elements, device memory of the vector type of
  * A->dtype; x and y must not overlap. Every element of y is written.
- * Mapping (the default of pjds_spmv_cfg): T threads per row, T in 1, 2, 4,
- * 8, from the longest row against the size of the product: with ratio =
+ * Mapping (the default of pjds_spmv_cfg): the per-tile mapping of A->plan
+ * when the longest row has more than 4 times the mean row length (and plan,
+ * val and col are 16-byte aligned); otherwise T threads per row for every
+ * row, T in 1, 2, 4, 8, from the longest row against the size of the
+ * product: with ratio =
  * n_max * 2^20 / (nnz * (value bytes + 4)), T = 1 below 2, 2 below 8, 4
  * below 64, else 8, then doubled (up to 8) while n_rows * T < 2^17. With
  * T = 1 each row sums in its original entry order; with T > 1 each lane sums
@@ -193,8 +211,18 @@ int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
  *                    gained and on widely spread row lengths the sorted
  *                    order's longest-first schedule is worth more, 5-25%).
  *                    The staged kernel always takes sorted order.
- * rows_per_thread > 1 and threads_per_row > 1 are exclusive. Invalid values
- * return PJDS_EINVAL.
+ *   plan             0: automatic, 1: the per-tile mapping of A->plan
+ *                    (PJDS_EINVAL if A->plan is NULL or plan, val or col is
+ *                    not 16-byte aligned), -1: a uniform mapping. Automatic
+ *                    uses the plan when it can and the longest row has more
+ *                    than 4 times the mean row length, unless the caller sets
+ *                    rows_per_thread, threads_per_row, block_threads, unroll,
+ *                    staged or tile_order (a uniform mapping asked for). On
+ *                    Zipf-distributed row lengths (1M-4M rows) the plan is
+ *                    1.0-1.6x as fast as the best uniform threads per row.
+ *                    With the plan the other fields do not apply.
+ * rows_per_thread > 1 and threads_per_row > 1 are exclusive, and staged
+ * excludes plan = 1. Invalid values return PJDS_EINVAL.
  */
 typedef struct pjds_launch {
   int32_t rows_per_thread;
@@ -205,7 +233,7 @@ typedef struct pjds_launch {
   int32_t index64;  /* 1: 64-bit element offsets even when 32 bits suffice (they are
                        used automatically from 2^31 stored entries on) */
   int32_t tile_order; /* 0 automatic, 1 the traversal table, -1 sorted order */
-  int32_t reserved;   /* 0 */
+  int32_t plan;       /* 0 automatic, 1 the per-tile mapping of A->plan, -1 a uniform mapping */
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
@@ -216,8 +244,9 @@ int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *
  * *out; nothing is launched and no device memory is touched. Fields left at 0
  * take defaults; rows_per_thread > 1 alone implies threads_per_row = 1 and
  * vice versa. out->tile_order is 1 (the table is used) or -1 (sorted order);
- * out->reserved is 0. Returns PJDS_EINVAL for a combination pjds_spmv_cfg
- * rejects.
+ * out->plan is 1 (the per-tile mapping; the other fields then describe the
+ * uniform mapping it replaces) or -1. Returns PJDS_EINVAL for a combination
+ * pjds_spmv_cfg rejects.
  */
 int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *out);
 

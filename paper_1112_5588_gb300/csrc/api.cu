@@ -19,6 +19,9 @@ static int check_pjds_dev(const pjds_dev *A, const void *x, const void *y, bool 
     return set_error(PJDS_EINVAL, "a matrix array is NULL");
   if (A->n_rows > 0 && !A->permute_cols && !A->perm) return set_error(PJDS_EINVAL, "perm is NULL");
   if (A->permute_cols && A->n_rows != A->n_cols) return set_error(PJDS_EINVAL, "permuted basis needs a square matrix");
+  // a plan holds at most one tile per 32 rows
+  if (A->plan && (A->n_plan < 0 || A->n_plan > A->n_pad / 32))
+    return set_error(PJDS_EINVAL, "n_plan %d outside [0, %d]", A->n_plan, A->n_pad / 32);
   return PJDS_OK;
 }
 
@@ -104,6 +107,7 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   c.staged = 0;
   c.index64 = 0;
   c.tile_order = auto_tile_order(A) ? 1 : 0;
+  c.plan = auto_plan(A) ? 1 : 0;
   return c;
 }
 
@@ -136,6 +140,18 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->tile_order < -1 || cfg->tile_order > 1) return set_error(PJDS_EINVAL, "tile_order must be -1, 0 or 1");
     if (cfg->tile_order == 1 && !A->tile_order) return set_error(PJDS_EINVAL, "tile_order = 1 but A->tile_order is NULL");
     if (cfg->tile_order) c.tile_order = cfg->tile_order == 1;
+    // the per-tile mapping: forced, switched off, or automatic unless the
+    // caller asked for a uniform mapping
+    if (cfg->plan < -1 || cfg->plan > 1) return set_error(PJDS_EINVAL, "plan must be -1, 0 or 1");
+    if (cfg->plan == 1) {
+      if (!plan_usable(A))
+        return set_error(PJDS_EINVAL, "plan = 1 needs A->plan with entries and 16-byte aligned plan, val and col");
+      if (cfg->staged) return set_error(PJDS_EINVAL, "staged and plan = 1 are exclusive");
+      c.plan = 1;
+    } else if (cfg->plan == -1 || cfg->rows_per_thread || cfg->threads_per_row || cfg->block_threads ||
+               cfg->unroll || cfg->staged || cfg->tile_order) {
+      c.plan = 0;
+    }
     if (cfg->staged) {
       c.staged = 1;
       if (!cfg->rows_per_thread) c.rows_per_thread = 1;
@@ -160,7 +176,7 @@ extern "C" int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds
   out->staged = c.staged;
   out->index64 = c.index64;
   out->tile_order = c.tile_order ? 1 : -1;
-  out->reserved = 0;
+  out->plan = c.plan ? 1 : -1;
   return PJDS_OK;
 }
 

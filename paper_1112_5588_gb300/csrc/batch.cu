@@ -9,11 +9,13 @@
 #include "common.h"
 #include "pjds_batch.h"
 #include "spmv_kernels.cuh"
+#include "plan.h"
+#include "tiles.cuh"
 
 namespace pjds {
 namespace bat {
 
-constexpr int BT = 256;  // threads per CTA; one batch tile = BT sorted rows
+using pjds::tiles::BT;  // threads per CTA
 
 // 16-byte vectors of the vector type
 template <typename TX>
@@ -105,154 +107,8 @@ __global__ void __launch_bounds__(BT)
 
 // ----------------------------------------------------------------------------- persistent batch
 
-struct Desc {
-  const void *val;
-  const int32_t *col;
-  const int64_t *col_start;
-  const int32_t *block_len;
-  const int32_t *perm;
-  const void *x;
-  void *y;
-  int32_t n_rows, b, scatter, idx64;
-};
+using namespace pjds::tiles;
 
-template <typename TV, typename TX, typename IDX>
-__device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int64_t i) {
-  using TA = typename dev::Acc<TV>::T;
-  constexpr int U = 4;
-  const TV *__restrict__ val = static_cast<const TV *>(d.val);
-  const TX *__restrict__ x = static_cast<const TX *>(d.x);
-  const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
-  TA acc = TA(0);
-  for (int32_t j = 0; j < L; j += U) {
-    int32_t c[U];
-    TV v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (j + u < L) {
-        const IDX o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
-        c[u] = __ldcs(d.col + o);
-        v[u] = dev::ld_stream1(val + o);
-      } else {
-        c[u] = -1;
-        v[u] = TV{};
-      }
-    }
-    TX xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = dev::gather(x, c[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
-  }
-  return acc;
-}
-
-// R adjacent sorted rows i .. i+R-1 (i a multiple of R: one block) with one
-// vector load of col and of val per jagged diagonal, U diagonals per round;
-// each row's arithmetic as in desc_row.
-template <typename TV, typename TX, typename IDX, int R, int U>
-__device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev::Acc<TV>::T (&acc)[R]) {
-  using TA = typename dev::Acc<TV>::T;
-  const TV *__restrict__ val = static_cast<const TV *>(d.val);
-  const TX *__restrict__ x = static_cast<const TX *>(d.x);
-  const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
-#pragma unroll
-  for (int r = 0; r < R; ++r) acc[r] = TA(0);
-  for (int32_t j = 0; j < L; j += U) {
-    int32_t c[U][R];
-    TV v[U][R];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (j + u < L) {
-        const IDX o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
-        dev::ld_stream<R>(d.col + o, c[u]);
-        dev::ld_stream<R>(val + o, v[u]);
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          c[u][r] = -1;
-          v[u][r] = TV{};
-        }
-      }
-    }
-    TX xv[U][R];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int r = 0; r < R; ++r) xv[u][r] = dev::gather(x, c[u][r]);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        acc[r] = c[u][r] >= 0 ? dev::fma_acc(dev::to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
-  }
-}
-
-// R adjacent rows per thread from the tile's first row; rows past the tile
-// or the matrix are not stored.
-template <typename TV, typename TX, int R, int U>
-__device__ __forceinline__ void rows_tile(const Desc &d, const int4 &tl, TX *y) {
-  const int32_t k = R * (int32_t)threadIdx.x;
-  const int64_t i = (int64_t)tl.y + k;
-  if (k >= tl.z || i >= d.n_rows) return;
-  typename dev::Acc<TV>::T acc[R];
-  if (d.idx64)
-    desc_rows<TV, TX, int64_t, R, U>(d, i, acc);
-  else
-    desc_rows<TV, TX, int32_t, R, U>(d, i, acc);
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (k + r < tl.z && i + r < d.n_rows) y[d.scatter ? (int64_t)__ldcs(d.perm + i + r) : i + r] = (TX)acc[r];
-}
-
-// LANES consecutive lanes share sorted row i: lane s takes jagged diagonals
-// s, s + LANES, ...; the partial sums are added with shuffles (fixed tree).
-template <typename TV, typename TX, typename IDX, int LANES>
-__device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d, int64_t i, int32_t s, bool active) {
-  using TA = typename dev::Acc<TV>::T;
-  constexpr int U = 4;
-  const TV *__restrict__ val = static_cast<const TV *>(d.val);
-  const TX *__restrict__ x = static_cast<const TX *>(d.x);
-  const int32_t L = active ? __ldg(d.block_len + (int32_t)(i / d.b)) : 0;
-  TA acc = TA(0);
-  for (int32_t j = s; j < L; j += U * LANES) {
-    int32_t c[U];
-    TV v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (j + u * LANES < L) {
-        const IDX o = (IDX)__ldg(d.col_start + j + u * LANES) + (IDX)i;
-        c[u] = __ldcs(d.col + o);
-        v[u] = dev::ld_stream1(val + o);
-      } else {
-        c[u] = -1;
-        v[u] = TV{};
-      }
-    }
-    TX xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = dev::gather(x, c[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
-  }
-#pragma unroll
-  for (int off = LANES / 2; off >= 1; off /= 2) acc += __shfl_down_sync(0xffffffffu, acc, off, LANES);
-  return acc;
-}
-
-// A tile of BT / LANES rows with LANES lanes each; the whole CTA stays for the
-// shuffles.
-template <typename TV, typename TX, int LANES>
-__device__ __forceinline__ void lanes_tile(const Desc &d, const int4 &tl, TX *y) {
-  const int32_t r = threadIdx.x / LANES, s = threadIdx.x % LANES;
-  const int64_t i = (int64_t)tl.y + r;
-  const bool active = r < tl.z && i < d.n_rows;
-  const auto acc = d.idx64 ? desc_row_lanes<TV, TX, int64_t, LANES>(d, i, s, active)
-                           : desc_row_lanes<TV, TX, int32_t, LANES>(d, i, s, active);
-  if (active && s == 0) y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
-}
-
-constexpr int MIN_TILE_ROWS = BT / 8;  // the smallest tile: 8 lanes per row
 
 // CTAs take tiles (matrix, first sorted row, rows, lanes per row) from a work
 // counter until none is left: tiles of one lane per row have one row per
@@ -271,24 +127,7 @@ __device__ __forceinline__ void
     if (t >= n_tiles) return;
     const int4 tl = tiles[t];
     const Desc d = descs[tl.x];
-    TX *y = static_cast<TX *>(d.y);
-    if (tl.w == 0) {  // two adjacent rows per thread
-      rows_tile<TV, TX, 2, 4>(d, tl, y);
-    } else if (tl.w == 3) {  // four adjacent rows per thread (rows of at most k_quad_max_len entries)
-      rows_tile<TV, TX, 4, 1>(d, tl, y);
-    } else if (tl.w == 1) {
-      const int64_t i = (int64_t)tl.y + threadIdx.x;
-      if ((int32_t)threadIdx.x < tl.z && i < d.n_rows) {
-        const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
-        y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
-      }
-    } else if (tl.w == 2) {
-      lanes_tile<TV, TX, 2>(d, tl, y);
-    } else if (tl.w == 4) {
-      lanes_tile<TV, TX, 4>(d, tl, y);
-    } else {
-      lanes_tile<TV, TX, 8>(d, tl, y);
-    }
+    run_tile<TV, TX>(d, tl);
   }
 }
 
@@ -407,9 +246,8 @@ extern "C" int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, v
 
 // ----------------------------------------------------------------------------- batch
 
-// upper bound of a matrix's tiles: every tile but the last one of a matrix
-// starts and ends on a multiple of MIN_TILE_ROWS
-static int64_t tiles_of(const pjds_dev &A) { return ((int64_t)A.n_rows + MIN_TILE_ROWS - 1) / MIN_TILE_ROWS; }
+// upper bound of a matrix's tiles (plan_cut)
+static int64_t tiles_of(const pjds_dev &A) { return plan_max_tiles(A.n_rows); }
 
 extern "C" int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_t *bytes) {
   clear_error();
@@ -422,13 +260,6 @@ extern "C" int pjds_batch_plan_bytes(int32_t n_mats, const pjds_dev *mats, size_
 
 // Plan: per matrix either fixed lanes (lanes[m] > 0) or the block-length
 // rule min_len (2, 4 or 8 lanes from block lengths min_len[0], [1], [2]).
-// Longest block (entries per row) whose rows a tile of the rule takes four at
-// a time per thread: on 64 Zipf matrices (9.8M rows, 61% of them with one
-// entry) 253 -> 237 us in fp64, 241 -> 214 us in fp32, 214 -> 208 us in bf16
-// against two rows per thread, with the same bits (thresholds 1 and 4 within
-// 1%).
-constexpr int32_t k_quad_max_len = 2;
-
 static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
                       const int32_t *lanes, const int32_t *min_len, void *plan_dev, size_t plan_bytes,
                       pjds_batch **out, void *stream) {
@@ -480,48 +311,15 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
     cudaError_t e = cudaMemcpyAsync(bl.data(), A.block_len, sizeof(int32_t) * bl.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(PJDS_ECUDA, "read block lengths: %s", cudaGetErrorString(e));
-    // long-row tiles first (blocks are sorted by length), then short-row
-    // tiles; or every tile with the matrix's given lanes per row
-    const int32_t fixed = lanes ? lanes[m] : 0;
     // one-lane tiles of the rule take two adjacent rows per thread when val
-    // and col allow the paired loads
+    // and col allow the paired loads, four when they allow 16-byte loads
+    const int32_t fixed = lanes ? lanes[m] : 0;
     const bool pair = !fixed && ((uintptr_t)A.val % (2 * value_bytes(dt))) == 0 && ((uintptr_t)A.col % 8) == 0;
-    // and four adjacent rows per thread for blocks of at most k_quad_max_len
-    // entries when val and col allow 16-byte loads
     const bool quad = pair && ((uintptr_t)A.val % 16) == 0 && ((uintptr_t)A.col % 16) == 0;
-    auto lanes_of = [&](int64_t L) -> int32_t {
-      return fixed ? fixed : L >= min_len[2] ? 8 : L >= min_len[1] ? 4 : L >= min_len[0] ? 2 : 1;
-    };
-    // tile kind: 8, 4 or 2 lanes per row, 1 (one row per thread), 0 (two
-    // rows per thread) or 3 (four rows per thread)
-    auto kind_of = [&](int64_t L) -> int32_t {
-      const int32_t ln = lanes_of(L);
-      if (ln != 1 || !pair) return ln;
-      return quad && L <= k_quad_max_len ? 3 : 0;
-    };
-    for (int64_t t0 = 0; t0 < A.n_rows;) {
-      const int32_t kind = kind_of(bl[(size_t)(t0 / A.b)]);
-      const int32_t ln = kind == 0 || kind == 3 ? 1 : kind;
-      const int32_t per_tile = kind == 3 ? 4 * BT : kind == 0 ? 2 * BT : BT / ln;
-      // a tile ends where its rows' blocks fall into another kind, so every
-      // row gets the mapping of its own block's length
-      int64_t end = std::min<int64_t>(t0 + per_tile, A.n_rows);
-      for (int64_t blk = t0 / A.b + 1; blk * A.b < end; ++blk)
-        if (kind_of(bl[(size_t)blk]) != kind) {
-          end = blk * A.b;
-          break;
-        }
-      const int64_t rows = end - t0;
-      // work estimate: stored entries of the tile's rows over the lanes per row
-      int64_t cost = 0;
-      for (int64_t r = t0; r < t0 + rows;) {
-        const int64_t blk = r / A.b, end = std::min<int64_t>((blk + 1) * A.b, t0 + rows);
-        cost += (end - r) * (int64_t)bl[(size_t)blk];
-        r = end;
-      }
-      tiles.push_back(T{m, (int32_t)t0, (int32_t)rows, kind, cost / ln});
-      t0 += rows;
-    }
+    const PlanRule rule = {{min_len[0], min_len[1], min_len[2]}, k_plan_rule.quad_max_len};
+    std::vector<PlanTile> cut;
+    plan_cut(A.n_rows, A.b, bl.data(), rule, fixed, pair, quad, cut);
+    for (const PlanTile &c : cut) tiles.push_back(T{m, c.row0, c.rows, c.kind, c.cost});
   }
   // matrices by total work per lane (largest first), tiles by work per lane
   // inside each matrix: the CTAs share one or two matrices' x at a time
@@ -577,7 +375,7 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
 // the built-in rule: 2 lanes per row from block length 16, 4 from 64, 8 from
 // 256 (the fastest of the tuner's candidate rules on 64 uneven Zipf
 // matrices: 253 us against 281 us for 8 lanes from 64 and one below)
-static const int32_t k_default_rule[3] = {16, 64, 256};
+static const int32_t k_default_rule[3] = {k_plan_rule.min_len[0], k_plan_rule.min_len[1], k_plan_rule.min_len[2]};
 
 extern "C" int pjds_batch_create(int32_t n_mats, const pjds_dev *mats, const void *const *xs, void *const *ys,
                                  void *plan_dev, size_t plan_bytes, pjds_batch **out, void *stream) {

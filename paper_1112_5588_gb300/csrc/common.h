@@ -33,4 +33,20 @@ inline bool auto_tile_order(const pjds_dev *A) {
   return (int64_t)A->n_max * A->n_rows <= 4 * A->nnz;
 }
 
+// Whether the per-tile mapping can run (a plan, 16-byte aligned plan, val and
+// col: the tiles of two and four rows per thread use vector loads).
+inline bool plan_usable(const pjds_dev *A) {
+  return A->plan && A->n_plan > 0 && (uintptr_t)A->plan % 16 == 0 && (uintptr_t)A->val % 16 == 0 &&
+         (uintptr_t)A->col % 16 == 0;
+}
+
+// Default use of the per-tile mapping: widely spread row lengths (the longest
+// row above 4 times the mean), where no single threads-per-row count suits
+// both the long and the short rows. On Zipf matrices of 1M-4M rows it ran
+// 1.0-1.6x as fast as the best uniform mapping; on the HMEp-like, stencil and
+// block-dense matrices the uniform mapping with the tile order stays faster.
+inline bool auto_plan(const pjds_dev *A) {
+  return plan_usable(A) && (int64_t)A->n_max * A->n_rows > 4 * A->nnz;
+}
+
 }  // namespace pjds

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.h"
+#include "plan.h"
 
 namespace pjds {
 
@@ -109,6 +110,7 @@ static void free_pjds(pjds_host *h) {
   free(h->col);
   free(h->val);
   free(h->tile_order);
+  free(h->plan);
   free(h);
 }
 
@@ -131,7 +133,7 @@ using namespace pjds;
 
 extern "C" const char *pjds_last_error(void) { return g_msg; }
 
-extern "C" int32_t pjds_version(void) { return 3; }
+extern "C" int32_t pjds_version(void) { return 4; }
 
 extern "C" void pjds_abi_sizes(int32_t out[5]) {
   out[0] = (int32_t)sizeof(pjds_host);
@@ -255,6 +257,27 @@ extern "C" int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_pt
     }
     std::stable_sort(h->tile_order, h->tile_order + n_tiles,
                      [&](int32_t a, int32_t c) { return key[(size_t)a] < key[(size_t)c]; });
+  }
+
+  // per-tile mapping: tiles of the default rule (pair and quad kinds assume
+  // 16-byte aligned device arrays; the launcher checks), by work per lane,
+  // largest first (stable)
+  {
+    std::vector<PlanTile> cut;
+    plan_cut(n_rows, b, h->block_len, k_plan_rule, 0, true, true, cut);
+    std::stable_sort(cut.begin(), cut.end(), [](const PlanTile &a, const PlanTile &c) { return a.cost > c.cost; });
+    h->n_plan = (int32_t)cut.size();
+    h->plan = alloc_n<int32_t>(4 * std::max<int64_t>((int64_t)cut.size(), 1));
+    if (!h->plan) {
+      free_pjds(h);
+      return set_error(PJDS_ENOMEM, "out of host memory");
+    }
+    for (size_t t = 0; t < cut.size(); ++t) {
+      h->plan[4 * t + 0] = 0;
+      h->plan[4 * t + 1] = cut[t].row0;
+      h->plan[4 * t + 2] = cut[t].rows;
+      h->plan[4 * t + 3] = cut[t].kind;
+    }
   }
   *out = h;
   return PJDS_OK;

@@ -4,9 +4,12 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.h"
 #include "spmv_kernels.cuh"
 #include "spmv_staged.cuh"
+#include "tiles.cuh"
 
 namespace pjds {
 
@@ -18,6 +21,7 @@ struct LaunchCfg {
   int staged;           // 1: bulk-copy staged persistent kernel (R = T = 1)
   int index64;          // 1: 64-bit element offsets regardless of size
   int tile_order;       // 1: tiles taken in A->tile_order
+  int plan;             // 1: per-tile mapping of A->plan (the fields above do not apply)
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -91,10 +95,35 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
   return check_launch("pjds_spmv launch");
 }
 
+// Per-tile mapping: one CTA per plan entry (tiles.cuh).
+template <typename TV, typename TX>
+int launch_plan(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaStream_t s) {
+  if (A->n_plan <= 0 || A->n_rows == 0) return PJDS_OK;
+  tiles::Desc d;
+  d.val = A->val;
+  d.col = A->col;
+  d.col_start = A->col_start;
+  d.block_len = A->block_len;
+  d.perm = A->perm;
+  d.x = x;
+  d.y = y;
+  d.n_rows = A->n_rows;
+  d.b = A->b;
+  d.scatter = A->permute_cols ? 0 : 1;
+  d.idx64 = c.index64 || A->n_stored + A->n_pad >= 0x7fffffffLL ? 1 : 0;
+  const int4 *plan = reinterpret_cast<const int4 *>(A->plan);
+  if constexpr (std::is_same<TV, double>::value)
+    tiles::pjds_plan_kernel_f64<<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
+  else
+    tiles::pjds_plan_kernel<TV, TX><<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
+  return check_launch("pjds_spmv plan launch");
+}
+
 template <typename TV, typename TX>
 int launch_pjds(const pjds_dev *A, const void *x, void *y, const LaunchCfg &c, cudaStream_t s) {
   const TX *xx = static_cast<const TX *>(x);
   TX *yy = static_cast<TX *>(y);
+  if (c.plan) return launch_plan<TV, TX>(A, xx, yy, c, s);
   const bool small = A->n_stored + A->n_pad < 0x7fffffffLL && !c.index64;
   const bool scatter = !A->permute_cols;
   if (small)

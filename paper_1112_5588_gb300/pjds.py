@@ -41,19 +41,20 @@ class _PjdsHostS(ctypes.Structure):
     _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("inv_perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp),
-                ("col", _vp), ("val", _vp), ("tile_order", _vp)]
+                ("col", _vp), ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32),
+                ("plan_reserved", _i32)]
 
 
 class _PjdsDevS(ctypes.Structure):
     _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp), ("col", _vp),
-                ("val", _vp), ("tile_order", _vp)]
+                ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32), ("plan_reserved", _i32)]
 
 
 class _LaunchS(ctypes.Structure):
     _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32),
-                ("staged", _i32), ("index64", _i32), ("tile_order", _i32), ("reserved", _i32)]
+                ("staged", _i32), ("index64", _i32), ("tile_order", _i32), ("plan", _i32)]
 
 
 class _EllrHostS(ctypes.Structure):
@@ -167,18 +168,23 @@ class PjdsHost:
         self.col = _np_view(s.col, s.n_stored, np.int32)
         self.val = _np_view(s.val, s.n_stored, _VAL_NP[s.dtype])
         self.tile_order = _np_view(s.tile_order, s.n_pad // 32, np.int32)
+        self.n_plan = int(s.n_plan)
+        # per-tile mapping: n_plan rows of (0, first sorted row, rows, kind)
+        self.plan = _np_view(s.plan, 4 * s.n_plan, np.int32).reshape(-1, 4)
 
     def arrays(self) -> dict:
         """Copies of every array plus the sizes (survive destroy())."""
         out = {k: getattr(self, k) for k, _ in _PjdsHostS._fields_[:10]}
-        for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val", "tile_order"):
+        for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val", "tile_order", "plan"):
             out[k] = getattr(self, k).copy()
+        out["n_plan"] = self.n_plan
         return out
 
-    def to_device(self, device="cuda", tile_order: bool = True) -> "PjdsDevice":
+    def to_device(self, device="cuda", tile_order: bool = True, plan: bool = True) -> "PjdsDevice":
         """Upload; tile_order=False leaves the traversal table out (tiles in
-        sorted order: same results, for comparisons)."""
-        return PjdsDevice(self, device, tile_order)
+        sorted order), plan=False the per-tile mapping (uniform mappings only):
+        same results, for comparisons."""
+        return PjdsDevice(self, device, tile_order, plan)
 
     def destroy(self):
         if self._ptr is not None:
@@ -207,7 +213,7 @@ def pjds_create(n_rows: int, n_cols: int, row_ptr, col, val, b: int = 32, dtype=
 class PjdsDevice:
     """Device copy of a pJDS matrix in torch-owned buffers plus its pjds_dev struct."""
 
-    def __init__(self, host: PjdsHost, device="cuda", tile_order: bool = True):
+    def __init__(self, host: PjdsHost, device="cuda", tile_order: bool = True, plan: bool = True):
         dev = torch.device(device)
         self.device = dev
         self.dtype = host.dtype
@@ -226,6 +232,8 @@ class PjdsDevice:
         self.col = up(host.col, np.int32)
         self.val = up(host.val, {0: np.float64, 1: np.float32, 2: np.int16}[host.dtype])
         self.tile_order = up(host.tile_order, np.int32) if tile_order else None
+        self.n_plan = host.n_plan if plan else 0
+        self.plan = up(host.plan, np.int32) if plan and host.n_plan > 0 else None
         s = _PjdsDevS()
         for f, _ in _PjdsDevS._fields_[:10]:
             setattr(s, f, getattr(host, f))
@@ -236,6 +244,8 @@ class PjdsDevice:
         s.col = self.col.data_ptr() or None
         s.val = self.val.data_ptr() or None
         s.tile_order = (self.tile_order.data_ptr() or None) if tile_order else None
+        s.plan = self.plan.data_ptr() if self.plan is not None else None
+        s.n_plan = self.n_plan if self.plan is not None else 0
         self._s = s
 
     @property
@@ -244,7 +254,8 @@ class PjdsDevice:
 
     def device_bytes(self) -> int:
         return sum(t.numel() * t.element_size() for t in (self.perm, self.block_len, self.row_len, self.col_start,
-                                                           self.col, self.val, self.tile_order) if t is not None)
+                                                           self.col, self.val, self.tile_order, self.plan)
+                   if t is not None)
 
 
 def _check_vec(t: torch.Tensor, n: int, dtype, name: str):
@@ -264,28 +275,29 @@ def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> t
 
 def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
                   threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, staged: int = 0,
-                  index64: int = 0, tile_order: int = 0, stream=None) -> torch.Tensor:
+                  index64: int = 0, tile_order: int = 0, plan: int = 0, stream=None) -> torch.Tensor:
     """y = A x with an explicit kernel configuration (pjds_spmv_cfg).
-    tile_order: 0 automatic, 1 traversal table, -1 sorted order."""
+    tile_order: 0 automatic, 1 traversal table, -1 sorted order; plan: 0
+    automatic, 1 the per-tile mapping, -1 a uniform mapping."""
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y
 
 
 def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, block_threads: int = 0,
-                      unroll: int = 0, staged: int = 0, index64: int = 0, tile_order: int = 0) -> dict:
+                      unroll: int = 0, staged: int = 0, index64: int = 0, tile_order: int = 0, plan: int = 0) -> dict:
     """The launch configuration pjds_spmv_cfg would use (no launch). `A` is a
     PjdsDevice or a PjdsHost (only sizes and alignment are read)."""
     s = A.struct if isinstance(A, PjdsDevice) else _dev_struct_from_host(A)
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan)
     out = _LaunchS()
     _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
             "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged,
-            "index64": out.index64, "tile_order": out.tile_order}
+            "index64": out.index64, "tile_order": out.tile_order, "plan": out.plan}
 
 
 def pjds_wait_selftest(which: int = 0, stream=None) -> None:
@@ -307,6 +319,8 @@ def _dev_struct_from_host(H: "PjdsHost"):
     # alignment of torch allocations (512 B) stands in for the device pointers
     s.val = s.col = s.col_start = s.block_len = s.perm = 512
     s.tile_order = 512 if len(H.tile_order) else None
+    s.plan = 512 if H.n_plan else None
+    s.n_plan = H.n_plan
     return s
 
 

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(P):
 
 
 def test_abi_version_and_struct_sizes(P):
-    assert P.lib().pjds_version() == 3  # the binding itself checked the struct sizes on load
+    assert P.lib().pjds_version() == 4  # the binding itself checked the struct sizes on load
 
 
 CASES = [
@@ -219,7 +219,7 @@ def test_resolve_defaults(P):
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
     # 10k rows: one thread per row would leave the GPU short of threads
     assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 8, "block_threads": 128, "unroll": 4,
-                                      "staged": 0, "index64": 0, "tile_order": -1}
+                                      "staged": 0, "index64": 0, "tile_order": -1, "plan": -1}
     # both sides of every threshold: the thread floor (2^17 rows at T = 1,
     # 2^16 at T = 2, ...) and the chain ratio (a long row of growing length)
     seen = set()
@@ -378,3 +378,85 @@ def test_batch_rule_checked_before_any_cuda_call(P):
     rc = Bt._lib.pjds_batch_tune_rule(1, s, (V * 1)(4096), (V * 1)(8192), (I * 3)(4, 16, 64), 1, 0, V(1 << 20),
                                       1 << 20, None, 0, us, ctypes.byref(best), None)
     assert rc == -1 and b"reps" in P.lib().pjds_last_error()
+
+
+# ----------------------------------------------------------------------------- per-tile mapping (plan)
+
+PLAN_CAP = {8: 32, 4: 64, 2: 128, 1: 256, 0: 512, 3: 1024}  # rows a tile of each kind maps
+
+
+def _plan_kind(L):
+    # 8 lanes from 256 entries, 4 from 64, 2 from 16; below: four rows per
+    # thread for blocks of at most 2 entries, else two
+    return 8 if L >= 256 else 4 if L >= 64 else 2 if L >= 16 else 3 if L <= 2 else 0
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.zipf_rows(20_011, s=1.8, len_max=700, seed=5),
+    lambda: tiny.random_lengths(1037, 900, max_len=300, seed=6, p_empty=0.3),
+    lambda: synth.hmep_like(n=5_000, seed=7),
+    lambda: tiny.constant_length(96, 70, 9, seed=1),
+    lambda: tiny.from_lengths([0] * 70, 5),
+    lambda: tiny.from_lengths([600] + [1] * 40 + [20] * 33, 700, seed=3),
+])
+@pytest.mark.parametrize("b", [32, 64])
+def test_plan_definition(P, make, b):
+    A = make()
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b)
+    plan, bl = H.plan, H.block_len
+    assert plan.shape == (H.n_plan, 4) and H.n_plan <= H.n_pad // 32
+    if A.n_rows == 0:
+        assert H.n_plan == 0
+        return
+    assert np.all(plan[:, 0] == 0) and np.all(plan[:, 2] > 0)
+    # the tiles partition the sorted rows, start on multiples of 32 and hold
+    # at most their kind's rows
+    by_row = plan[np.argsort(plan[:, 1])]
+    assert by_row[0, 1] == 0 and np.array_equal(by_row[1:, 1], by_row[:-1, 1] + by_row[:-1, 2])
+    assert by_row[-1, 1] + by_row[-1, 2] == A.n_rows
+    assert np.all(by_row[:, 1] % 32 == 0)
+    for row0, rows, kind in by_row[:, 1:]:
+        assert rows <= PLAN_CAP[int(kind)]
+        kinds = {_plan_kind(int(bl[k])) for k in range(row0 // b, (row0 + rows - 1) // b + 1)}
+        assert kinds == {int(kind)}, (row0, rows, kind, kinds)
+    # a tile ends early only at the matrix's end or where the kind changes
+    for (row0, rows, kind), nxt in zip(by_row[:, 1:], list(by_row[1:, 1:]) + [None]):
+        if rows < PLAN_CAP[int(kind)] and nxt is not None:
+            assert nxt[2] != kind or _plan_kind(int(bl[(row0 + rows) // b])) != kind
+    # entries by work per lane, largest first
+    def cost(row0, rows, kind):
+        lanes = 1 if kind in (0, 3) else kind
+        blocks = np.arange(row0, row0 + rows) // b
+        return int(bl[blocks].astype(np.int64).sum()) // lanes
+    costs = [cost(*map(int, e[1:])) for e in plan]
+    assert all(c0 >= c1 for c0, c1 in zip(costs, costs[1:]))
+
+
+def test_plan_resolve(P):
+    Z = synth.zipf_rows(50_000, s=2.0, len_max=512, seed=8)     # longest row >> 4 x mean
+    HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
+    M = synth.hmep_like(n=50_000, seed=9)                        # longest row < 4 x mean
+    HM = P.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32)
+    assert P.pjds_spmv_resolve(HZ)["plan"] == 1
+    assert P.pjds_spmv_resolve(HM)["plan"] == -1
+    assert P.pjds_spmv_resolve(HM, plan=1)["plan"] == 1
+    # asking for a uniform mapping switches the plan off
+    for kw in (dict(threads_per_row=2), dict(rows_per_thread=2), dict(block_threads=128), dict(unroll=4),
+               dict(staged=1), dict(tile_order=-1), dict(plan=-1)):
+        assert P.pjds_spmv_resolve(HZ, **kw)["plan"] == -1, kw
+    assert P.pjds_spmv_resolve(HZ, index64=1)["plan"] == 1
+    for bad in (dict(plan=2), dict(plan=-2), dict(plan=1, staged=1)):
+        with pytest.raises(P.PjdsError):
+            P.pjds_spmv_resolve(HZ, **bad)
+    # no plan, or arrays the vector loads cannot take: automatic falls back,
+    # forcing is an error
+    for field, value in (("plan", None), ("col", 516), ("val", 520), ("plan", 520)):
+        s = P._dev_struct_from_host(HZ)
+        setattr(s, field, value)
+        out = P._LaunchS()
+        assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(out)) == 0 and out.plan == -1, field
+        cfg = P._LaunchS(0, 0, 0, 0, 0, 0, 0, 1)
+        assert P.lib().pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)) == -1, field
+    s = P._dev_struct_from_host(HZ)
+    s.n_plan = s.n_pad // 32 + 1
+    assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(P._LaunchS())) == -1

@@ -63,7 +63,8 @@ def test_spmv_and_ellr_write_only_y(mods, dtype, permute):
             x = torch.rand(A.n_cols, device="cuda", dtype=D.vec_dtype)
             for cfg in (dict(), dict(threads_per_row=1), dict(threads_per_row=8, block_threads=64),
                         dict(rows_per_thread=2), dict(rows_per_thread=4), dict(staged=1), dict(tile_order=1),
-                        dict(rows_per_thread=2, tile_order=1), dict(threads_per_row=4, tile_order=1)):
+                        dict(rows_per_thread=2, tile_order=1), dict(threads_per_row=4, tile_order=1),
+                        dict(plan=1), dict(plan=1, index64=1)):
                 raw, y = guarded(torch, A.n_rows, D.vec_dtype)
                 pjds.pjds_spmv_cfg(D, x, y, **cfg)
                 torch.cuda.synchronize()

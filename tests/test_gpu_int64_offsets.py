@@ -110,7 +110,7 @@ def _oracle_rows(oracle_lib, rows):
 
 
 @pytest.mark.parametrize("cfg", [None, dict(rows_per_thread=1), dict(threads_per_row=4), dict(tile_order=-1),
-                                 dict(staged=1), "ellr"])
+                                 dict(staged=1), dict(plan=1), "ellr"])
 def test_offsets_beyond_2_31_exact(big, oracle_lib, cfg):
     import torch
     pjds, D, E, x, _ = big

@@ -76,6 +76,7 @@ CONFIGS = [
     dict(threads_per_row=1, unroll=4), dict(threads_per_row=1, unroll=16), dict(rows_per_thread=2, unroll=8), dict(rows_per_thread=2, unroll=2),
     dict(rows_per_thread=4, unroll=4), dict(threads_per_row=4, unroll=2), dict(threads_per_row=2, block_threads=32),
     dict(staged=1), dict(index64=1), dict(threads_per_row=4, index64=1), dict(rows_per_thread=2, index64=1),
+    dict(plan=1), dict(plan=1, index64=1),
 ]
 CONFIG_SHAPES = [SHAPES[1], SHAPES[4], SHAPES[6]]
 
@@ -273,8 +274,8 @@ def test_tile_order_bitwise_equal_to_sorted_order(P, dtype, b, permute):
                     dict(threads_per_row=8, block_threads=64), dict(), dict(index64=1), dict(rows_per_thread=2, index64=1)):
             yo = torch.full((A.n_rows,), float("nan"), dtype=Do.vec_dtype, device="cuda")
             yn = torch.full_like(yo, float("nan"))
-            P.pjds_spmv_cfg(Do, x, yo, tile_order=1, **cfg)
-            P.pjds_spmv_cfg(Dn, x, yn, **cfg)
+            P.pjds_spmv_cfg(Do, x, yo, tile_order=1, plan=-1, **cfg)
+            P.pjds_spmv_cfg(Dn, x, yn, plan=-1, **cfg)
             torch.cuda.synchronize()
             assert torch.equal(yo.view(torch.int16 if dtype != "f64" else torch.int64),
                                yn.view(torch.int16 if dtype != "f64" else torch.int64)), (cfg, A.n_rows)
@@ -333,3 +334,48 @@ def test_host_stream_equals_single_products(P, dtype, permute):
     P.pjds_spmv_host_stream(D, xs[:1], y1, xd, yd)
     assert torch.equal(y1[0], ys[0])
     P.pjds_spmv_host_stream(D, [], [], xd, yd)
+
+
+PLAN_SHAPES = [
+    ("zipf_wide", lambda: synth.zipf_rows(50_000, s=1.6, len_max=1024, seed=21)),
+    ("ragged_long", lambda: tiny.from_lengths([700, 300, 90, 17] + [1, 2, 5, 30] * 300 + [0] * 40, 1500, seed=22)),
+    ("one_full_row", lambda: tiny.one_full_row(900, full_row=11)),
+    ("ragged_tail", lambda: tiny.random_lengths(1037, 1037, max_len=70, seed=23, p_empty=0.15)),
+]
+
+
+@pytest.mark.parametrize("name,make", PLAN_SHAPES, ids=[s[0] for s in PLAN_SHAPES])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("permute", [False, True])
+def test_plan_rows_bit_identical_to_uniform_mappings(P, name, make, dtype, permute):
+    # each row of the per-tile mapping is summed as the uniform mapping with
+    # its tile's lanes per row sums it (one thread per row for kinds 0, 1, 3)
+    torch = _torch()
+    A = make()
+    if permute and A.n_rows != A.n_cols:
+        pytest.skip("permuted basis needs a square matrix")
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype, permute_cols=permute)
+    D = H.to_device("cuda")
+    xt = torch.from_numpy(synth.vector(A.n_cols, seed=24)).to(device="cuda", dtype=D.vec_dtype)
+
+    def run(**cfg):
+        y = torch.full((A.n_rows,), float("nan"), dtype=D.vec_dtype, device="cuda")
+        P.pjds_spmv_cfg(D, xt, y, **cfg)
+        torch.cuda.synchronize()
+        return y.cpu().numpy()
+
+    y_plan = run(plan=1)
+    uniform = {t: run(threads_per_row=t, plan=-1) for t in (1, 2, 4, 8)}
+    lanes = np.zeros(H.n_pad, np.int64)
+    for _, row0, rows, kind in H.plan:
+        lanes[row0:row0 + rows] = 1 if kind in (0, 1, 3) else kind
+    assert np.all(lanes[:A.n_rows] > 0)
+    out = np.arange(A.n_rows) if permute else H.perm.astype(np.int64)
+    want = np.empty_like(y_plan)
+    for t in (1, 2, 4, 8):
+        rows = out[lanes[:A.n_rows] == t]
+        want[rows] = uniform[t][rows]
+    assert np.array_equal(y_plan.view(np.uint8), want.view(np.uint8))
+    # the default takes the plan exactly when the row lengths are widely spread
+    spread = H.n_max * A.n_rows > 4 * A.nnz
+    assert P.pjds_spmv_resolve(D)["plan"] == (1 if spread else -1)
