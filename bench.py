@@ -289,6 +289,7 @@ def run_ours(args, world, rank, local_rank):
         side["side"]["batching"] = batching_leg(torch, pjds, args, dev, flush)
         side["side"]["small_case"] = small_case_leg(torch, pjds, args, dev, flush)
         side["side"]["tuning"] = tuning_leg(torch, pjds, args, dev)
+        side["side"]["spread"] = spread_leg(torch, pjds, args, dev, flush)
 
     # ---------------- end to end through the C ABI from pinned host memory: K
     # products in one pjds_spmv_host_stream call (each step copies its x in
@@ -754,6 +755,37 @@ def tuning_leg(torch, pjds, args, dev):
             "default_mapping": pjds.pjds_spmv_resolve(D), "default_us": round(t_def, 2),
             "learned_pick": f"b{pick['b']}_T{pick['threads_per_row']}", "learned_pick_us": t_pick,
             "best_speedup_over_paper_mapping": round(paper / us[best_key], 3)}
+
+
+def spread_leg(torch, pjds, args, dev, flush):
+    """Widely spread row lengths (sAMG-like: Zipf s = 2, rows of 1 to 512
+    entries, 1M rows; fp64 and fp32): the per-tile mapping pjds_spmv takes
+    for such a matrix against every uniform threads-per-row count, L2 flushed
+    before each launch."""
+    med = statistics.median
+    import synth
+    A = synth.zipf_rows(1_000_000, s=2.0, len_max=512, seed=args.seed)
+    lens = np.diff(A.row_ptr)
+    out = {"matrix": f"Zipf s=2 N={A.n_rows} nnz={A.nnz} (rows up to {int(lens.max())}, mean {lens.mean():.2f})"}
+    for dt, vb, xb in (("f64", 8, 8), ("f32", 4, 4)):
+        H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dt)
+        D = H.to_device(dev)
+        n_plan = H.n_plan
+        H.destroy()
+        x = torch.from_numpy(synth.vector(A.n_cols, seed=args.seed)).to(dev, D.vec_dtype)
+        y = torch.empty(A.n_rows, dtype=D.vec_dtype, device=dev)
+        nb = alg_bytes(A.n_rows, A.n_cols, A.nnz, vb, xb)
+        t_def = med(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 20, 3, flush))
+        uni = {t: med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, x, y, threads_per_row=t, plan=-1), 20, 3, flush))
+               for t in (1, 2, 4, 8)}
+        best = min(uni, key=uni.get)
+        out[dt] = {"default_uses_plan": pjds.pjds_spmv_resolve(D)["plan"] == 1, "plan_tiles": n_plan,
+                   "default_us": round(t_def * 1e6, 2), "default_gbs": round(nb / t_def / 1e9, 1),
+                   "uniform_us": {f"T{t}": round(v * 1e6, 2) for t, v in uni.items()},
+                   "best_uniform": f"T{best}", "speedup_vs_best_uniform": round(uni[best] / t_def, 3)}
+        del D, x, y
+    torch.cuda.synchronize()
+    return out
 
 
 def precision_oracle_checks(oracle, pg):
