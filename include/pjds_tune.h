@@ -32,7 +32,9 @@ typedef struct pjds_candidate {
   int32_t block_threads;   /* as in pjds_launch (0 = default) */
   int32_t unroll;          /* as in pjds_launch (0 = default) */
   int32_t staged;          /* as in pjds_launch */
-  int32_t reserved;
+  int32_t plan;            /* as in pjds_launch: 1 times the per-tile mapping of
+                              the matrix's plan (the fields above then do not
+                              apply); 0 with uniform fields set means -1 */
 } pjds_candidate;
 
 typedef struct pjds_tune_entry {
@@ -45,8 +47,9 @@ typedef struct pjds_tune_entry {
 
 /*
  * Device arena bytes the sweep over `cands` needs for this CRS matrix: the
- * largest pJDS matrix among the candidates' (b, dtype) pairs plus x and y of
- * the widest vector type, each array 256-byte aligned.
+ * largest pJDS matrix among the candidates' (b, dtype) pairs (with its
+ * traversal table and plan) plus x and y of the widest vector type, each
+ * array 256-byte aligned.
  */
 int pjds_tune_arena_bytes(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const pjds_candidate *cands,
                           int32_t n_cands, size_t *bytes);

@@ -49,7 +49,7 @@ static Shape shape_for(int32_t n_rows, const int64_t *row_ptr, int32_t b) {
 static size_t matrix_bytes(const Shape &s, int32_t n_rows, int32_t dtype) {
   return a256((size_t)n_rows * 4) + a256((size_t)s.n_blocks * 4) + a256((size_t)(s.n_max + 1) * 8) +
          a256((size_t)s.n_stored * 4) + a256((size_t)s.n_stored * value_bytes(dtype)) +
-         a256((size_t)(s.n_pad / 32) * 4);
+         a256((size_t)(s.n_pad / 32) * 4) + a256((size_t)(s.n_pad / 32) * 16);
 }
 
 static size_t arena_need(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const pjds_candidate *c,
@@ -166,6 +166,8 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
     d.col = static_cast<const int32_t *>(place(h->col, (size_t)h->n_stored * 4));
     d.val = place(h->val, (size_t)h->n_stored * value_bytes(dt));
     d.tile_order = static_cast<const int32_t *>(place(h->tile_order, (size_t)(h->n_pad / 32) * 4));
+    d.plan = static_cast<const int32_t *>(place(h->plan, (size_t)h->n_plan * 16));
+    d.n_plan = h->n_plan;
     void *x = p;
     p += a256((size_t)n_cols * 8);
     void *y = p;
@@ -187,6 +189,7 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
       in.threads_per_row = cands[i].threads_per_row;
       in.block_threads = cands[i].block_threads;
       in.unroll = cands[i].unroll;
+      in.plan = cands[i].plan;
       const int r = pjds_spmv_resolve(&d, &in, &res);
       out[i].n_stored = n_stored;
       if (r != PJDS_OK) {
@@ -198,6 +201,7 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
       out[i].cand.block_threads = res.block_threads;
       out[i].cand.unroll = res.unroll;
       out[i].cand.staged = res.staged;
+      out[i].cand.plan = res.plan;
       std::vector<float> t((size_t)reps);
       int lr = PJDS_OK;
       for (int w = 0; w < 2 && lr == PJDS_OK; ++w) lr = pjds_spmv_cfg(&d, x, y, &res, stream);

@@ -17,7 +17,7 @@ DTYPE_NAMES = {0: "f64", 1: "f32", 2: "bf16"}
 
 class _Cand(ctypes.Structure):
     _fields_ = [("b", _i32), ("dtype", _i32), ("rows_per_thread", _i32), ("threads_per_row", _i32),
-                ("block_threads", _i32), ("unroll", _i32), ("staged", _i32), ("reserved", _i32)]
+                ("block_threads", _i32), ("unroll", _i32), ("staged", _i32), ("plan", _i32)]
 
 
 class _Entry(ctypes.Structure):
@@ -36,18 +36,23 @@ for _name, _args in (("pjds_tune_arena_bytes", [_i32, _i32, _vp, _P(_Cand), _i32
 def _cand_dict(c) -> dict:
     return {"b": c.b, "dtype": DTYPE_NAMES.get(c.dtype, c.dtype), "rows_per_thread": c.rows_per_thread,
             "threads_per_row": c.threads_per_row, "block_threads": c.block_threads, "unroll": c.unroll,
-            "staged": c.staged}
+            "staged": c.staged, "plan": c.plan}
 
 
-def default_space(dtypes=("f64",)) -> list:
-    """b in {32,64,128,256} x threads per row in {1,2,4,8} x dtypes."""
+def default_space(dtypes=("f64",), plan: bool = False) -> list:
+    """b in {32,64,128,256} x threads per row in {1,2,4,8} x dtypes; with
+    plan=True also the per-tile mapping for every b and dtype."""
     mask = 0
     for d in dtypes:
         mask |= 1 << _p.DTYPES[d]
     buf = (_Cand * 64)()
     n = _i32()
     _p._check(_lib.pjds_tune_default_space(mask, buf, 64, ctypes.byref(n)), "pjds_tune_default_space")
-    return [_cand_dict(buf[i]) for i in range(n.value)]
+    out = [_cand_dict(buf[i]) for i in range(n.value)]
+    if plan:
+        out += [{"b": b, "dtype": d, "rows_per_thread": 0, "threads_per_row": 0, "block_threads": 0, "unroll": 0,
+                 "staged": 0, "plan": 1} for d in dtypes for b in (32, 64, 128, 256)]
+    return out
 
 
 def _to_cands(cands) -> ctypes.Array:
@@ -55,7 +60,7 @@ def _to_cands(cands) -> ctypes.Array:
     for i, c in enumerate(cands):
         arr[i] = _Cand(int(c["b"]), _p._dtype_code(c.get("dtype", "f64")), int(c.get("rows_per_thread", 0)),
                        int(c.get("threads_per_row", 0)), int(c.get("block_threads", 0)), int(c.get("unroll", 0)),
-                       int(c.get("staged", 0)), 0)
+                       int(c.get("staged", 0)), int(c.get("plan", 0)))
     return arr
 
 

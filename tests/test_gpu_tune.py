@@ -55,3 +55,27 @@ def test_sweep_and_best_candidate_parity(mods, oracle_lib):
         xd = x.astype(np.float32).astype(np.float64)
         r = parity.check_fp32(yo, oracle_lib.crs_spmv(Ar, xd), oracle_lib.crs_absmv(Ar, xd), np.diff(A.row_ptr))
     assert r["ok"], (e, r)
+
+
+def test_sweep_times_the_per_tile_mapping(mods, oracle_lib):
+    # plan candidates run the matrix's per-tile mapping; on widely spread rows
+    # (Zipf s = 2, 1M rows: 1.4-1.7x over the best uniform count) it wins
+    torch, pjds, tune = mods
+    A = synth.zipf_rows(1_000_000, s=2.0, len_max=512, seed=6)
+    cands = tune.default_space(("f64",), plan=True)
+    assert sum(c.get("plan", 0) == 1 for c in cands) == 4 and len(cands) == 20
+    entries, best = tune.sweep(A, cands, reps=7)
+    for c, e in zip(cands, entries):
+        assert e["status"] == 0 and e["us"] > 0, e
+        assert e["plan"] == (1 if c.get("plan") == 1 else -1), (c, e)
+    assert entries[best]["plan"] == 1, [(e["b"], e["threads_per_row"], e["plan"], round(e["us"], 1)) for e in entries]
+    # the winning candidate's product against the oracle
+    e = entries[best]
+    H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=e["b"], dtype="f64")
+    D = H.to_device("cuda")
+    x = synth.vector(A.n_cols, seed=6)
+    y = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
+    pjds.pjds_spmv_cfg(D, torch.from_numpy(x).cuda(), y, plan=1)
+    torch.cuda.synchronize()
+    r = parity.check_fp64(y.cpu().numpy(), oracle_lib.crs_spmv(A, x), oracle_lib.crs_absmv(A, x), np.diff(A.row_ptr))
+    assert r["ok"], r

@@ -37,6 +37,7 @@ def test_arena_bytes_covers_every_candidate(T, make):
         H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=c["b"], dtype=c["dtype"])
         vb = {"f64": 8, "f32": 4, "bf16": 2}[c["dtype"]]
         m = a256(4 * H.n_rows) + a256(4 * H.n_blocks) + a256(8 * (H.n_max + 1)) + a256(4 * H.n_stored) + \
-            a256(vb * H.n_stored) + a256(4 * (H.n_pad // 32))
+            a256(vb * H.n_stored) + a256(4 * (H.n_pad // 32)) + a256(16 * (H.n_pad // 32))
+        assert 16 * H.n_plan <= 16 * (H.n_pad // 32)  # the plan's room: one entry per 32 rows at most
         worst = max(worst, m)
     assert need == worst + a256(8 * A.n_cols) + a256(8 * A.n_rows)
