@@ -186,9 +186,6 @@ __device__ __forceinline__ void run_tile(const Desc &d, const int4 &tl) {
   }
 }
 
-// Per-tile mapping of one product: CTA k takes plan entry k. The entries are
-// ordered by their work per lane, largest first, so the block scheduler
-// starts the long tiles first and fills in with short ones.
 // An entry outside the matrix, of an unknown kind, with more rows than its
 // kind maps, or of two or four rows per thread on a first row that is not a
 // multiple of 2 or 4 (vector loads) does not describe a tile: it is skipped.
@@ -205,6 +202,9 @@ __device__ __forceinline__ bool plan_entry_ok(const int4 &tl, int32_t n_pad) {
   }
 }
 
+// Per-tile mapping of one product: CTA k takes plan entry k. The entries are
+// ordered by their work per lane, largest first, so the block scheduler
+// starts the long tiles first and fills in with short ones.
 template <typename TV, typename TX>
 __global__ void __launch_bounds__(BT) pjds_plan_kernel(const Desc d, const int4 *__restrict__ plan, int32_t n_pad) {
   const int4 tl = plan[blockIdx.x];
