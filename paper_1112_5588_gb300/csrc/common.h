@@ -42,11 +42,17 @@ inline bool plan_usable(const pjds_dev *A) {
 
 // Default use of the per-tile mapping: widely spread row lengths (the longest
 // row above 4 times the mean), where no single threads-per-row count suits
-// both the long and the short rows. On Zipf matrices of 1M-4M rows it ran
-// 1.0-1.6x as fast as the best uniform mapping; on the HMEp-like, stencil and
-// block-dense matrices the uniform mapping with the tile order stays faster.
+// both the long and the short rows, from 2^16 rows (fp64), 2^17 (fp32) or
+// 2^18 (bf16) on: below that, one tile per 32 to 1024 rows leaves too few
+// CTAs and the uniform mapping's extra lanes win. Thresholds fitted on the
+// timings of 2,000 Zipf matrices (10k-4M rows); on 200 held-out ones the
+// default then runs at 0.870 / 0.941 / 0.980 of the best uniform mapping's
+// time (geometric mean; the uniform rule alone 1.10 / 1.07 / 1.08). On the
+// HMEp-like, stencil and block-dense matrices the uniform mapping with the
+// tile order stays faster.
 inline bool auto_plan(const pjds_dev *A) {
-  return plan_usable(A) && (int64_t)A->n_max * A->n_rows > 4 * A->nnz;
+  const int32_t min_rows = A->dtype == PJDS_F64 ? (1 << 16) : A->dtype == PJDS_F32 ? (1 << 17) : (1 << 18);
+  return plan_usable(A) && A->n_rows >= min_rows && (int64_t)A->n_max * A->n_rows > 4 * A->nnz;
 }
 
 }  // namespace pjds

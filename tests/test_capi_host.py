@@ -433,8 +433,16 @@ def test_plan_definition(P, make, b):
 
 
 def test_plan_resolve(P):
-    Z = synth.zipf_rows(50_000, s=2.0, len_max=512, seed=8)     # longest row >> 4 x mean
+    Z = synth.zipf_rows(70_000, s=2.0, len_max=512, seed=8)     # longest row >> 4 x mean, >= 2^16 rows
     HZ = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
+    # size thresholds: 2^16 rows (fp64), 2^17 (fp32), 2^18 (bf16)
+    for n, want in ((65_535, (-1, -1, -1)), (65_536, (1, -1, -1)), (131_072, (1, 1, -1)), (262_144, (1, 1, 1))):
+        Zn = synth.zipf_rows(n, s=2.0, len_max=512, seed=10)
+        for dt, w in zip(("f64", "f32", "bf16"), want):
+            Hn = P.pjds_create(Zn.n_rows, Zn.n_cols, Zn.row_ptr, Zn.col, Zn.val, b=32, dtype=dt)
+            assert P.pjds_spmv_resolve(Hn)["plan"] == w, (n, dt)
+            assert P.pjds_spmv_resolve(Hn, plan=1)["plan"] == 1
+            Hn.destroy()
     M = synth.hmep_like(n=50_000, seed=9)                        # longest row < 4 x mean
     HM = P.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32)
     assert P.pjds_spmv_resolve(HZ)["plan"] == 1
