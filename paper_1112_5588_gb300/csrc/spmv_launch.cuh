@@ -113,7 +113,7 @@ int launch_plan(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaS
   d.idx64 = c.index64 || A->n_stored + A->n_pad >= 0x7fffffffLL ? 1 : 0;
   const int4 *plan = reinterpret_cast<const int4 *>(A->plan);
   if constexpr (std::is_same<TV, double>::value)
-    tiles::pjds_plan_kernel_f64<<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
+    tiles::pjds_plan_kernel_f64<><<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
   else
     tiles::pjds_plan_kernel<TV, TX><<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
   return check_launch("pjds_spmv plan launch");

@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(BT) pjds_plan_kernel(const Desc d, const int4 
 // fp64 values: bounded to six resident CTAs per SM (40 registers; unbounded
 // the instance takes 42, allocated as 48: five CTAs per SM). fp32 and bf16
 // stay unbounded (40 and 34 registers).
-static __global__ void __launch_bounds__(BT, 6)
+template <int = 0>  // a template: instantiated only where it is launched
+__global__ void __launch_bounds__(BT, 6)
     pjds_plan_kernel_f64(const Desc d, const int4 *__restrict__ plan, int32_t n_pad) {
   const int4 tl = plan[blockIdx.x];
   if (!plan_entry_ok(tl, n_pad)) return;
