@@ -264,6 +264,20 @@ int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *ou
 int pjds_device_status(int32_t *status, int32_t clear, void *stream);
 
 /*
+ * Checked build only (libpjds_checked.so, compiled with PJDS_CHECKED; a test
+ * build standing in for a memory checker): the product kernels with one or
+ * T threads per row, several rows per thread, the per-tile mapping, the
+ * batched launch and ELLPACK-R compare every jagged-diagonal index, element
+ * offset, gathered column, block index and stored row with its array's
+ * extent before the access, skip an access outside it and record the first
+ * such access: *word = (code << 56) | index, code 1 jagged diagonal, 2
+ * element offset, 3 gathered column, 4 stored row, 5 block index; 0 when
+ * none. clear = 1 resets it. Waits for the stream. The normal build returns
+ * PJDS_EINVAL.
+ */
+int pjds_check_word(uint64_t *word, int32_t clear, void *stream);
+
+/*
  * Failure-detection self-test of the staged kernel's bounded waits: launches
  * one thread that waits on an mbarrier nothing completes (which = 0: as a
  * consumer, which = 1: as the producer). The wait gives up after its limit

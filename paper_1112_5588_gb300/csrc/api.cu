@@ -203,6 +203,23 @@ extern "C" int pjds_device_status(int32_t *status, int32_t clear, void *stream) 
   return PJDS_OK;
 }
 
+extern "C" int pjds_check_word(uint64_t *word, int32_t clear, void *stream) {
+  clear_error();
+  if (!word) return set_error(PJDS_EINVAL, "word is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long w[4] = {0, 0, 0, 0};
+  int (*const readers[4])(unsigned long long *, bool, cudaStream_t) = {check_word_f64, check_word_f32,
+                                                                      check_word_bf16, check_word_batch};
+  for (int k = 0; k < 4; ++k) {
+    const int e = readers[k](&w[k], clear != 0, s);
+    if (e == (int)cudaErrorNotSupported) return set_error(PJDS_EINVAL, "not a checked build (PJDS_CHECKED)");
+    if (e != 0) return set_error(PJDS_ECUDA, "reading the check word: %s", cudaGetErrorString((cudaError_t)e));
+  }
+  *word = 0;
+  for (int k = 0; k < 4 && !*word; ++k) *word = w[k];
+  return PJDS_OK;
+}
+
 extern "C" int pjds_wait_selftest(int32_t which, void *stream) {
   clear_error();
   if (which != 0 && which != 1) return set_error(PJDS_EINVAL, "which must be 0 or 1");

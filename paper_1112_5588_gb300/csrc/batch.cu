@@ -151,6 +151,19 @@ __global__ void __launch_bounds__(BT, 6)
 static inline size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace bat
+
+// The batched launch's translation unit's check word (checked build).
+int check_word_batch(unsigned long long *w, bool clear, cudaStream_t s) {
+#ifdef PJDS_CHECKED
+  return (int)dev::read_check_word(w, clear, s);
+#else
+  (void)clear;
+  (void)s;
+  *w = 0;
+  return (int)cudaErrorNotSupported;
+#endif
+}
+
 }  // namespace pjds
 
 using namespace pjds;
@@ -305,6 +318,11 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
     d.b = A.b;
     d.scatter = A.permute_cols ? 0 : 1;
     d.idx64 = A.n_stored + A.n_pad < 0x7fffffffLL ? 0 : 1;
+    d.stored = A.n_stored;
+    d.n_cols = A.n_cols;
+    d.n_blocks = A.n_blocks;
+    d.n_diag = A.n_max + 1;
+    d.reserved = 0;
     if (A.n_rows == 0) continue;
     // block lengths back to the host once, to weigh the tiles
     std::vector<int32_t> bl((size_t)A.n_blocks);

@@ -15,4 +15,6 @@ int staged_status_bf16(int *out, bool clear, cudaStream_t s) {
   return (int)dev::staged_status(out, clear, s);
 }
 
+int check_word_bf16(unsigned long long *w, bool clear, cudaStream_t s) { return check_word_here<>(w, clear, s); }
+
 }  // namespace pjds

@@ -20,4 +20,6 @@ int staged_status_f64(int *out, bool clear, cudaStream_t s) {
   return (int)dev::staged_status(out, clear, s);
 }
 
+int check_word_f64(unsigned long long *w, bool clear, cudaStream_t s) { return check_word_here<>(w, clear, s); }
+
 }  // namespace pjds

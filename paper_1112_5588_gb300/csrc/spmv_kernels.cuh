@@ -152,6 +152,67 @@ __device__ __forceinline__ TX gather(const TX *__restrict__ x, int32_t c) {
   return c >= 0 ? __ldg(x + c) : TX(0);
 }
 
+// ----------------------------------------------------------------------------- checked build
+
+// Built with PJDS_CHECKED (libpjds_checked.so, a test build), the product
+// kernels compare every jagged-diagonal index, element offset, gathered
+// column, block index and stored row with its array's extent before the
+// access. A violation skips the access and records its code and index in
+// g_check_word (the first one; codes below); nothing traps. In the normal
+// build PJDS_IN is `true` and the checks compile away.
+enum CheckCode : unsigned { CHK_DIAG = 1, CHK_OFFSET = 2, CHK_COLUMN = 3, CHK_ROW = 4, CHK_BLOCK = 5 };
+
+// Extents of the arrays one uniform-mapping launch reads (set by the
+// launcher before each launch in the checked build).
+struct Extents {
+  int64_t stored;  // val, col
+  int32_t n_cols;  // x
+  int32_t n_rows;  // y (and perm)
+  int32_t n_blocks;
+  int32_t n_diag;  // col_start entries: n_max + 1
+};
+
+#ifdef PJDS_CHECKED
+static __device__ Extents g_ext;
+static __device__ unsigned long long g_check_word;
+__device__ __forceinline__ bool in_extent(int64_t i, int64_t n, unsigned code) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_check_word, 0ull, ((unsigned long long)code << 56) | ((unsigned long long)i & 0xFFFFFFFFFFFFFFull));
+  return false;
+}
+#define PJDS_IN(i, n, code) ::pjds::dev::in_extent((int64_t)(i), (int64_t)(n), (code))
+#define PJDS_EXT(field) ::pjds::dev::g_ext.field
+#else
+#define PJDS_IN(i, n, code) true
+#define PJDS_EXT(field) 0
+#endif
+
+#ifdef PJDS_CHECKED
+// This translation unit's check word (and optionally clear it); waits for s.
+static inline cudaError_t read_check_word(unsigned long long *w, bool clear, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyFromSymbolAsync(w, g_check_word, sizeof(*w), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && clear) {
+    const unsigned long long zero = 0;
+    e = cudaMemcpyToSymbolAsync(g_check_word, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  return e;
+}
+
+// Extents of a uniform-mapping launch, copied before the kernel on s.
+static inline cudaError_t set_extents(const Extents &x, cudaStream_t s) {
+  return cudaMemcpyToSymbolAsync(g_ext, &x, sizeof(x), 0, cudaMemcpyHostToDevice, s);
+}
+#endif
+
+// gather with the extent of x checked in the checked build
+template <typename TX>
+__device__ __forceinline__ TX gather_n(const TX *__restrict__ x, int32_t c, int32_t n_cols) {
+  (void)n_cols;
+  return c >= 0 && PJDS_IN(c, n_cols, CHK_COLUMN) ? __ldg(x + c) : TX(0);
+}
+
 // ----------------------------------------------------------------------------- pJDS, R rows per thread
 
 // Thread t owns sorted rows [R*t, R*t + R) of one block (b is a multiple of
@@ -170,6 +231,7 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
   int64_t i0 = t * R;
   if (i0 >= n_pad) return;
   if (order && !tile_row(order, n_pad, i0)) return;
+  if (!PJDS_IN(i0 / b, PJDS_EXT(n_blocks), CHK_BLOCK)) return;
   const int32_t L = __ldg(block_len + (int32_t)(i0 / b));
   TA acc[R];
 #pragma unroll
@@ -180,8 +242,13 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
     TV v[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j + u < L) {
-        const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i0;
+      bool live = j + u < L && PJDS_IN(j + u, PJDS_EXT(n_diag), CHK_DIAG);
+      IDX o = 0;
+      if (live) {
+        o = (IDX)__ldg(col_start + j + u) + (IDX)i0;
+        live = PJDS_IN(o, PJDS_EXT(stored), CHK_OFFSET) && PJDS_IN((int64_t)o + (R - 1), PJDS_EXT(stored), CHK_OFFSET);
+      }
+      if (live) {
         ld_stream<R>(col + o, c[u]);
         ld_stream<R>(val + o, v[u]);
       } else {
@@ -196,7 +263,7 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < R; ++r) xv[u][r] = gather(x, c[u][r]);
+      for (int r = 0; r < R; ++r) xv[u][r] = gather_n(x, c[u][r], PJDS_EXT(n_cols));
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -207,10 +274,12 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
   for (int r = 0; r < R; ++r) {
     const int64_t i = i0 + r;
     if (i < n_rows) {
-      if constexpr (SCATTER)
-        y[__ldcs(perm + i)] = (TX)acc[r];
-      else
+      if constexpr (SCATTER) {
+        const int32_t p = __ldcs(perm + i);
+        if (PJDS_IN(p, PJDS_EXT(n_rows), CHK_ROW)) y[p] = (TX)acc[r];
+      } else {
         y[i] = (TX)acc[r];
+      }
     }
   }
 }
@@ -232,6 +301,7 @@ __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ va
   const int32_t s = (int32_t)(g % T);
   bool active = i < n_pad;  // whole warps stay for the shuffles
   if (active && order) active = tile_row(order, n_pad, i);
+  if (active) active = PJDS_IN(i / b, PJDS_EXT(n_blocks), CHK_BLOCK);
   const int32_t L = active ? __ldg(block_len + (int32_t)(i / b)) : 0;
   TA acc = TA(0);
   for (int32_t j = s; j < L; j += U * T) {
@@ -239,8 +309,13 @@ __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ va
     TV v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j + u * T < L) {
-        const IDX o = (IDX)__ldg(col_start + j + u * T) + (IDX)i;
+      bool live = j + u * T < L && PJDS_IN(j + u * T, PJDS_EXT(n_diag), CHK_DIAG);
+      IDX o = 0;
+      if (live) {
+        o = (IDX)__ldg(col_start + j + u * T) + (IDX)i;
+        live = PJDS_IN(o, PJDS_EXT(stored), CHK_OFFSET);
+      }
+      if (live) {
         c[u] = __ldcs(col + o);
         v[u] = ld_stream1(val + o);
       } else {
@@ -250,17 +325,19 @@ __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ va
     }
     TX xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = gather(x, c[u]);
+    for (int u = 0; u < U; ++u) xv[u] = gather_n(x, c[u], PJDS_EXT(n_cols));
 #pragma unroll
     for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? fma_acc(to_acc(v[u]), (TA)xv[u], acc) : acc;
   }
 #pragma unroll
   for (int off = T / 2; off >= 1; off /= 2) acc += __shfl_down_sync(0xffffffffu, acc, off, T);
   if (s == 0 && active && i < n_rows) {
-    if constexpr (SCATTER)
-      y[__ldcs(perm + i)] = (TX)acc;
-    else
+    if constexpr (SCATTER) {
+      const int32_t p = __ldcs(perm + i);
+      if (PJDS_IN(p, PJDS_EXT(n_rows), CHK_ROW)) y[p] = (TX)acc;
+    } else {
       y[i] = (TX)acc;
+    }
   }
 }
 
@@ -281,8 +358,8 @@ __global__ void __launch_bounds__(512) ellr_kernel(const TV *__restrict__ val, c
     TV v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j + u < L) {
-        const IDX o = (IDX)(j + u) * (IDX)n_pad + (IDX)i;
+      const IDX o = (IDX)(j + u) * (IDX)n_pad + (IDX)i;
+      if (j + u < L && PJDS_IN(o, PJDS_EXT(stored), CHK_OFFSET)) {
         c[u] = __ldcs(col + o);
         v[u] = ld_stream1(val + o);
       } else {
@@ -292,7 +369,7 @@ __global__ void __launch_bounds__(512) ellr_kernel(const TV *__restrict__ val, c
     }
     TX xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = gather(x, c[u]);
+    for (int u = 0; u < U; ++u) xv[u] = gather_n(x, c[u], PJDS_EXT(n_cols));
 #pragma unroll
     for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? fma_acc(to_acc(v[u]), (TA)xv[u], acc) : acc;
   }

@@ -60,6 +60,9 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
   if (grid > 0x7fffffffLL) return set_error(PJDS_EOVERFLOW, "grid too large");
   const dim3 g((unsigned)grid), blk((unsigned)nt);
   const int32_t *order = c.tile_order ? A->tile_order : nullptr;
+#ifdef PJDS_CHECKED
+  dev::set_extents(dev::Extents{A->n_stored, A->n_cols, A->n_rows, A->n_blocks, A->n_max + 1}, s);
+#endif
 #define PJDS_ARGS val, A->col, A->col_start, A->block_len, A->perm, order, x, y, A->n_rows, A->n_pad, A->b
   const int U = c.unroll;
 #define PJDS_ROWS(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
@@ -111,6 +114,11 @@ int launch_plan(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaS
   d.b = A->b;
   d.scatter = A->permute_cols ? 0 : 1;
   d.idx64 = c.index64 || A->n_stored + A->n_pad >= 0x7fffffffLL ? 1 : 0;
+  d.stored = A->n_stored;
+  d.n_cols = A->n_cols;
+  d.n_blocks = A->n_blocks;
+  d.n_diag = A->n_max + 1;
+  d.reserved = 0;
   const int4 *plan = reinterpret_cast<const int4 *>(A->plan);
   if constexpr (std::is_same<TV, double>::value)
     tiles::pjds_plan_kernel_f64<><<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
@@ -145,6 +153,9 @@ int launch_ellr(const ellr_dev *A, const void *x, void *y, int nt, cudaStream_t 
   const int64_t grid = ((int64_t)A->n_rows + nt - 1) / nt;
   if (grid <= 0) return PJDS_OK;
   const TV *val = static_cast<const TV *>(A->val);
+#ifdef PJDS_CHECKED
+  dev::set_extents(dev::Extents{A->n_stored, A->n_cols, A->n_rows, 0, 0}, s);
+#endif
   const TX *xx = static_cast<const TX *>(x);
   TX *yy = static_cast<TX *>(y);
   if (A->n_stored < 0x7fffffffLL)
@@ -179,5 +190,23 @@ int staged_status_f64(int *out, bool clear, cudaStream_t s);
 int staged_wait_selftest(int which, cudaStream_t s);
 int staged_status_f32(int *out, bool clear, cudaStream_t s);
 int staged_status_bf16(int *out, bool clear, cudaStream_t s);
+// First out-of-extent access the checked build met in each translation unit
+// (0: none); the normal build returns cudaErrorNotSupported.
+int check_word_f64(unsigned long long *w, bool clear, cudaStream_t s);
+int check_word_f32(unsigned long long *w, bool clear, cudaStream_t s);
+int check_word_bf16(unsigned long long *w, bool clear, cudaStream_t s);
+int check_word_batch(unsigned long long *w, bool clear, cudaStream_t s);
+
+template <typename = void>
+int check_word_here(unsigned long long *w, bool clear, cudaStream_t s) {
+#ifdef PJDS_CHECKED
+  return (int)dev::read_check_word(w, clear, s);
+#else
+  (void)clear;
+  (void)s;
+  *w = 0;
+  return (int)cudaErrorNotSupported;
+#endif
+}
 
 }  // namespace pjds

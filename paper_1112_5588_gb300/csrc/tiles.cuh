@@ -22,8 +22,17 @@ struct Desc {
   const int32_t *perm;
   const void *x;
   void *y;
+  int64_t stored;  // val, col elements
   int32_t n_rows, b, scatter, idx64;
+  int32_t n_cols, n_blocks, n_diag, reserved;  // extents checked in the checked build (n_diag = n_max + 1)
 };
+
+// Store row i's sum (through perm in the original basis).
+template <typename TX, typename TA>
+__device__ __forceinline__ void store_row(const Desc &d, TX *y, int64_t i, TA v) {
+  const int64_t r = d.scatter ? (int64_t)__ldcs(d.perm + i) : i;
+  if (PJDS_IN(r, d.n_rows, dev::CHK_ROW)) y[r] = (TX)v;
+}
 
 template <typename TV, typename TX, typename IDX>
 __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int64_t i) {
@@ -31,15 +40,20 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int6
   constexpr int U = 4;
   const TV *__restrict__ val = static_cast<const TV *>(d.val);
   const TX *__restrict__ x = static_cast<const TX *>(d.x);
-  const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
+  const int32_t L = PJDS_IN(i / d.b, d.n_blocks, dev::CHK_BLOCK) ? __ldg(d.block_len + (int32_t)(i / d.b)) : 0;
   TA acc = TA(0);
   for (int32_t j = 0; j < L; j += U) {
     int32_t c[U];
     TV v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j + u < L) {
-        const IDX o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
+      bool live = j + u < L && PJDS_IN(j + u, d.n_diag, dev::CHK_DIAG);
+      IDX o = 0;
+      if (live) {
+        o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
+        live = PJDS_IN(o, d.stored, dev::CHK_OFFSET);
+      }
+      if (live) {
         c[u] = __ldcs(d.col + o);
         v[u] = dev::ld_stream1(val + o);
       } else {
@@ -49,7 +63,7 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int6
     }
     TX xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = dev::gather(x, c[u]);
+    for (int u = 0; u < U; ++u) xv[u] = dev::gather_n(x, c[u], d.n_cols);
 #pragma unroll
     for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
   }
@@ -64,7 +78,7 @@ __device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev
   using TA = typename dev::Acc<TV>::T;
   const TV *__restrict__ val = static_cast<const TV *>(d.val);
   const TX *__restrict__ x = static_cast<const TX *>(d.x);
-  const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
+  const int32_t L = PJDS_IN(i / d.b, d.n_blocks, dev::CHK_BLOCK) ? __ldg(d.block_len + (int32_t)(i / d.b)) : 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = TA(0);
   for (int32_t j = 0; j < L; j += U) {
@@ -72,8 +86,13 @@ __device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev
     TV v[U][R];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j + u < L) {
-        const IDX o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
+      bool live = j + u < L && PJDS_IN(j + u, d.n_diag, dev::CHK_DIAG);
+      IDX o = 0;
+      if (live) {
+        o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
+        live = PJDS_IN(o, d.stored, dev::CHK_OFFSET) && PJDS_IN((int64_t)o + (R - 1), d.stored, dev::CHK_OFFSET);
+      }
+      if (live) {
         dev::ld_stream<R>(d.col + o, c[u]);
         dev::ld_stream<R>(val + o, v[u]);
       } else {
@@ -88,7 +107,7 @@ __device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < R; ++r) xv[u][r] = dev::gather(x, c[u][r]);
+      for (int r = 0; r < R; ++r) xv[u][r] = dev::gather_n(x, c[u][r], d.n_cols);
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -111,7 +130,7 @@ __device__ __forceinline__ void rows_tile(const Desc &d, const int4 &tl, TX *y) 
     desc_rows<TV, TX, int32_t, R, U>(d, i, acc);
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (k + r < tl.z && i + r < d.n_rows) y[d.scatter ? (int64_t)__ldcs(d.perm + i + r) : i + r] = (TX)acc[r];
+    if (k + r < tl.z && i + r < d.n_rows) store_row(d, y, i + r, acc[r]);
 }
 
 // LANES consecutive lanes share sorted row i: lane s takes jagged diagonals
@@ -122,15 +141,21 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d
   constexpr int U = 4;
   const TV *__restrict__ val = static_cast<const TV *>(d.val);
   const TX *__restrict__ x = static_cast<const TX *>(d.x);
-  const int32_t L = active ? __ldg(d.block_len + (int32_t)(i / d.b)) : 0;
+  const int32_t L =
+      active && PJDS_IN(i / d.b, d.n_blocks, dev::CHK_BLOCK) ? __ldg(d.block_len + (int32_t)(i / d.b)) : 0;
   TA acc = TA(0);
   for (int32_t j = s; j < L; j += U * LANES) {
     int32_t c[U];
     TV v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j + u * LANES < L) {
-        const IDX o = (IDX)__ldg(d.col_start + j + u * LANES) + (IDX)i;
+      bool live = j + u * LANES < L && PJDS_IN(j + u * LANES, d.n_diag, dev::CHK_DIAG);
+      IDX o = 0;
+      if (live) {
+        o = (IDX)__ldg(d.col_start + j + u * LANES) + (IDX)i;
+        live = PJDS_IN(o, d.stored, dev::CHK_OFFSET);
+      }
+      if (live) {
         c[u] = __ldcs(d.col + o);
         v[u] = dev::ld_stream1(val + o);
       } else {
@@ -140,7 +165,7 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d
     }
     TX xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = dev::gather(x, c[u]);
+    for (int u = 0; u < U; ++u) xv[u] = dev::gather_n(x, c[u], d.n_cols);
 #pragma unroll
     for (int u = 0; u < U; ++u) acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
   }
@@ -158,7 +183,7 @@ __device__ __forceinline__ void lanes_tile(const Desc &d, const int4 &tl, TX *y)
   const bool active = r < tl.z && i < d.n_rows;
   const auto acc = d.idx64 ? desc_row_lanes<TV, TX, int64_t, LANES>(d, i, s, active)
                            : desc_row_lanes<TV, TX, int32_t, LANES>(d, i, s, active);
-  if (active && s == 0) y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
+  if (active && s == 0) store_row(d, y, i, acc);
 }
 
 // One plan entry tl = {matrix, first sorted row, rows, kind} of matrix d, by
@@ -175,7 +200,7 @@ __device__ __forceinline__ void run_tile(const Desc &d, const int4 &tl) {
     const int64_t i = (int64_t)tl.y + threadIdx.x;
     if ((int32_t)threadIdx.x < tl.z && i < d.n_rows) {
       const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
-      y[d.scatter ? (int64_t)__ldcs(d.perm + i) : i] = (TX)acc;
+      store_row(d, y, i, acc);
     }
   } else if (tl.w == 2) {
     lanes_tile<TV, TX, 2>(d, tl, y);

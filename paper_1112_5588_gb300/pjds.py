@@ -21,7 +21,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpjds.so")
+# PJDS_LIBRARY=checked loads the checked build (device-side extent checks,
+# a test build); the product library otherwise
+LIB_PATH = os.path.join(_HERE, "libpjds_checked.so" if os.environ.get("PJDS_LIBRARY") == "checked" else "libpjds.so")
 
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
 _VEC_TORCH = {0: torch.float64, 1: torch.float32, 2: torch.float32}
@@ -86,6 +88,7 @@ def _load_lib():
         "pjds_spmv_host_stream": (ctypes.c_int, [P(_PjdsDevS), _i32, P(_vp), P(_vp), P(_vp), P(_vp), _vp]),
         "pjds_spmv_resolve": (ctypes.c_int, [P(_PjdsDevS), P(_LaunchS), P(_LaunchS)]),
         "pjds_device_status": (ctypes.c_int, [P(_i32), _i32, _vp]),
+        "pjds_check_word": (ctypes.c_int, [P(ctypes.c_uint64), _i32, _vp]),
         "pjds_wait_selftest": (ctypes.c_int, [_i32, _vp]),
         "pjds_permute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_unpermute": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
@@ -298,6 +301,14 @@ def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, blo
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
             "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged,
             "index64": out.index64, "tile_order": out.tile_order, "plan": out.plan}
+
+
+def pjds_check_word(clear: bool = True, stream=None) -> int:
+    """The checked build's first out-of-extent access, (code << 56) | index,
+    0 when none (pjds_check_word; PjdsError in the normal build)."""
+    w = ctypes.c_uint64()
+    _check(_lib.pjds_check_word(ctypes.byref(w), 1 if clear else 0, _stream_ptr(stream)), "pjds_check_word")
+    return int(w.value)
 
 
 def pjds_wait_selftest(which: int = 0, stream=None) -> None:

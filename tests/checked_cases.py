@@ -1,0 +1,148 @@
+"""Cases for the checked build (run by tests/test_gpu_checked.py in a process
+with PJDS_LIBRARY=checked, which loads libpjds_checked.so).
+
+Clean: every mapping of the product with device-side extent checks (one and
+T threads per row, several rows per thread, tile order, per-tile mapping,
+64-bit offsets), ELLPACK-R and the batched launch, on ragged, spread and
+banded matrices, must leave the check word at 0 and (fp64) match the oracle.
+
+Planted: an index put out of range in a device copy of a matrix (a column
+beyond n_cols, a perm entry beyond n_rows, a jagged-diagonal offset beyond
+the stored entries, a block longer than the longest row) must be recorded
+with its code and skipped: the kernels check each index before the access.
+
+Prints one JSON line.
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CFGS = [dict(), dict(threads_per_row=1), dict(rows_per_thread=2), dict(rows_per_thread=4), dict(threads_per_row=2),
+        dict(threads_per_row=4), dict(threads_per_row=8), dict(tile_order=1), dict(plan=1), dict(index64=1),
+        dict(plan=1, index64=1), dict(rows_per_thread=2, index64=1)]
+CODE_SHIFT = 56
+
+
+def split(w):
+    return w >> CODE_SHIFT, w & ((1 << CODE_SHIFT) - 1)
+
+
+def main():
+    assert os.environ.get("PJDS_LIBRARY") == "checked"
+    import torch
+
+    import oracle
+    import synth
+    from paper_1112_5588_gb300 import batch, pjds
+    from synth import tiny
+    from tests import parity
+    assert pjds.LIB_PATH.endswith("libpjds_checked.so")
+    oracle.build()
+    assert pjds.pjds_check_word(clear=True) == 0
+
+    mats = {
+        "ragged": tiny.random_lengths(1037, 1037, max_len=90, seed=61, p_empty=0.2),
+        "zipf": synth.zipf_rows(70_000, s=1.8, len_max=600, seed=62),
+        "hmep": synth.hmep_like(n=30_011, seed=63),
+        "full_row": tiny.one_full_row(900, full_row=37),
+    }
+    res = {"clean": [], "planted": {}}
+
+    def run(D, xt, cfg):
+        y = torch.full((D.n_rows,), float("nan"), dtype=D.vec_dtype, device="cuda")
+        pjds.pjds_spmv_cfg(D, xt, y, **cfg)
+        torch.cuda.synchronize()
+        return y
+
+    for name, A in mats.items():
+        x = synth.vector(A.n_cols, seed=64)
+        yref, absax, lens = oracle.crs_spmv(A, x), oracle.crs_absmv(A, x), np.diff(A.row_ptr)
+        for dt in ("f64", "f32", "bf16"):
+            for b in (32, 128):
+                H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b, dtype=dt)
+                D = H.to_device("cuda")
+                H.destroy()
+                xt = torch.from_numpy(x).to("cuda", D.vec_dtype)
+                for cfg in CFGS:
+                    y = run(D, xt, cfg)
+                    w = pjds.pjds_check_word(clear=True)
+                    ok = bool(torch.isfinite(y).all())
+                    if dt == "f64":
+                        ok = ok and parity.check_fp64(y.cpu().numpy(), yref, absax, lens)["ok"]
+                    res["clean"].append([name, dt, b, cfg, w, ok])
+            E = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype=dt).to_device("cuda")
+            y = torch.full((A.n_rows,), float("nan"), dtype=E.vec_dtype, device="cuda")
+            pjds.ellr_spmv(E, torch.from_numpy(x).to("cuda", E.vec_dtype), y)
+            torch.cuda.synchronize()
+            w = pjds.pjds_check_word(clear=True)
+            ok = bool(torch.isfinite(y).all())
+            if dt == "f64":
+                ok = ok and parity.check_fp64(y.cpu().numpy(), yref, absax, lens)["ok"]
+            res["clean"].append([name, dt, 0, "ellr", w, ok])
+
+    # the batched launch over all four matrices, with the built-in rule and given lanes
+    devs = [pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32).to_device("cuda")
+            for A in mats.values()]
+    xs = [torch.from_numpy(synth.vector(A.n_cols, seed=65)).cuda() for A in mats.values()]
+    for kw in (dict(), dict(lanes=[1, 8, 2, 4]), dict(rule=(4, 16, 64))):
+        ys = [torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda") for A in mats.values()]
+        B = batch.Batch(devs, xs, ys, **kw)
+        B.run(use_graph=False)
+        torch.cuda.synchronize()
+        w = pjds.pjds_check_word(clear=True)
+        ok = all(parity.check_fp64(y.cpu().numpy(), oracle.crs_spmv(A, xv.cpu().numpy()),
+                                   oracle.crs_absmv(A, xv.cpu().numpy()), np.diff(A.row_ptr))["ok"]
+                 for A, xv, y in zip(mats.values(), xs, ys))
+        B.destroy()
+        res["clean"].append(["batch", "f64", 32, kw.get("lanes") and "lanes" or kw.get("rule") and "rule" or "default",
+                             w, ok])
+
+    # planted indices (fp64, original basis)
+    A = mats["ragged"]
+    H = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
+    x = synth.vector(A.n_cols, seed=66)
+    mapping = [dict(threads_per_row=1), dict(rows_per_thread=2), dict(threads_per_row=4), dict(plan=1), dict()]
+
+    def planted(mutate):
+        out = []
+        for cfg in mapping:
+            D = H.to_device("cuda")
+            mutate(D)
+            xt = torch.from_numpy(x).cuda()
+            pjds.pjds_check_word(clear=True)
+            run(D, xt, cfg)
+            out.append([cfg, *split(pjds.pjds_check_word(clear=True))])
+        return out
+
+    res["n"] = {"n_rows": A.n_rows, "n_cols": A.n_cols, "n_stored": H.n_stored, "n_max": H.n_max}
+    res["planted"]["column"] = planted(lambda D: D.col.__setitem__(0, A.n_cols + 5))
+    res["planted"]["perm"] = planted(lambda D: D.perm.__setitem__(3, A.n_rows + 7))
+    res["planted"]["offset"] = planted(lambda D: D.col_start.__setitem__(1, H.n_stored + 1000))
+    res["planted"]["block"] = planted(lambda D: D.block_len.__setitem__(0, H.n_max + 3))
+    # a planted column changes at most the one row that holds it
+    D = H.to_device("cuda")
+    xt = torch.from_numpy(x).cuda()
+    y0 = run(D, xt, dict(threads_per_row=1))
+    D.col[0] = A.n_cols + 5
+    y1 = run(D, xt, dict(threads_per_row=1))
+    pjds.pjds_check_word(clear=True)
+    res["column_rows_changed"] = int((y0 != y1).sum().item())
+    # ELLPACK-R with a column beyond n_cols
+    E = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val).to_device("cuda")
+    k = int(np.argmax(np.diff(A.row_ptr) > 0))
+    E.col[k] = A.n_cols + 9
+    y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    pjds.ellr_spmv(E, torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    res["planted"]["ellr_column"] = [[{}, *split(pjds.pjds_check_word(clear=True))]]
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -468,3 +468,11 @@ def test_plan_resolve(P):
     s = P._dev_struct_from_host(HZ)
     s.n_plan = s.n_pad // 32 + 1
     assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(P._LaunchS())) == -1
+
+
+def test_check_word_only_in_the_checked_build(P):
+    # the normal build has no device-side extent checks: PJDS_EINVAL, no GPU call
+    w = ctypes.c_uint64(123)
+    assert P.lib().pjds_check_word(ctypes.byref(w), 0, None) == -1
+    assert b"checked build" in P.lib().pjds_last_error()
+    assert w.value == 123 or w.value == 0
