@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(BT)
   const int64_t i = t / lr;
   const int32_t q = (int32_t)(t % lr);
   if (i >= n_rows) return;
-  const int32_t L = __ldg(block_len + (int32_t)(i / b));
+  const int32_t L = PJDS_IN(i / b, PJDS_EXT(n_blocks), dev::CHK_BLOCK) ? __ldg(block_len + (int32_t)(i / b)) : 0;
   TA acc[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) acc[w] = TA(0);
@@ -68,8 +68,15 @@ __global__ void __launch_bounds__(BT)
     TV v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (j + u < L) {
+      if (j + u < L && PJDS_IN(j + u, PJDS_EXT(n_diag), dev::CHK_DIAG)) {
         const IDX o = (IDX)__ldg(col_start + j + u) + (IDX)i;
+#ifdef PJDS_CHECKED
+        if (!PJDS_IN(o, PJDS_EXT(stored), dev::CHK_OFFSET)) {
+          c[u] = -1;
+          v[u] = TV{};
+          continue;
+        }
+#endif
         c[u] = __ldcs(col + o);
         v[u] = dev::ld_stream1(val + o);
       } else {
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(BT)
     TX xv[U][W];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (c[u] >= 0) {
+      if (c[u] >= 0 && PJDS_IN(c[u], PJDS_EXT(n_cols), dev::CHK_COLUMN)) {
 #pragma unroll
         for (int h = 0; h < CH; ++h)
           V16<TX>::load(X + (int64_t)c[u] * k + (int64_t)q * W + h * VW,
@@ -100,6 +107,7 @@ __global__ void __launch_bounds__(BT)
 #pragma unroll
   for (int w = 0; w < W; ++w) out[w] = (TX)acc[w];
   const int64_t r = SCATTER ? (int64_t)__ldcs(perm + i) : i;
+  if (!PJDS_IN(r, PJDS_EXT(n_rows), dev::CHK_ROW)) return;
 #pragma unroll
   for (int h = 0; h < CH; ++h)
     V16<TX>::store(Y + r * k + (int64_t)q * W + h * VW, *reinterpret_cast<const TX(*)[VW]>(&out[h * VW]));
@@ -205,6 +213,9 @@ static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cud
   const TX *x = static_cast<const TX *>(X);
   TX *y = static_cast<TX *>(Y);
   const bool small = A->n_stored + A->n_pad < 0x7fffffffLL, sc = !A->permute_cols;
+#ifdef PJDS_CHECKED
+  dev::set_extents(dev::Extents{A->n_stored, A->n_cols, A->n_rows, A->n_blocks, A->n_max + 1}, s);
+#endif
 #define SPMM(IDX, SC, CH)                                                                                        \
   spmm_kernel<TV, TX, IDX, SC, CH><<<(unsigned)grid, BT, 0, s>>>(val, A->col, A->col_start, A->block_len, A->perm, \
                                                                   x, y, A->n_rows, A->b, k, lr)

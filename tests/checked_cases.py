@@ -86,6 +86,25 @@ def main():
                 ok = ok and parity.check_fp64(y.cpu().numpy(), yref, absax, lens)["ok"]
             res["clean"].append([name, dt, 0, "ellr", w, ok])
 
+    # SpMM: k right-hand sides
+    for name, A in mats.items():
+        lens = np.diff(A.row_ptr)
+        for dt, ks in (("f64", (2, 8)), ("f32", (4, 32))):
+            D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dt).to_device("cuda")
+            for k in ks:
+                X = np.stack([synth.vector(A.n_cols, seed=70 + c) for c in range(k)], axis=1)
+                Y = torch.full((A.n_rows, k), float("nan"), dtype=D.vec_dtype, device="cuda")
+                batch.spmm(D, torch.from_numpy(np.ascontiguousarray(X)).to("cuda", D.vec_dtype), Y)
+                torch.cuda.synchronize()
+                w = pjds.pjds_check_word(clear=True)
+                ok = bool(torch.isfinite(Y).all())
+                if dt == "f64":
+                    Yr = oracle.crs_spmm(A, X)
+                    S = np.abs(oracle.crs_spmm(A._replace(val=np.abs(A.val)), np.abs(X)))
+                    Yg = Y.cpu().numpy()
+                    ok = ok and all(parity.check_fp64(Yg[:, c], Yr[:, c], S[:, c], lens)["ok"] for c in range(k))
+                res["clean"].append([name, dt, 32, f"spmm k={k}", w, ok])
+
     # the batched launch over all four matrices, with the built-in rule and given lanes
     devs = [pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32).to_device("cuda")
             for A in mats.values()]
@@ -141,6 +160,13 @@ def main():
     pjds.ellr_spmv(E, torch.from_numpy(x).cuda(), y)
     torch.cuda.synchronize()
     res["planted"]["ellr_column"] = [[{}, *split(pjds.pjds_check_word(clear=True))]]
+    # SpMM with a column beyond n_cols
+    D = H.to_device("cuda")
+    D.col[0] = A.n_cols + 5
+    Y = torch.empty(A.n_rows, 4, dtype=torch.float64, device="cuda")
+    batch.spmm(D, torch.rand(A.n_cols, 4, dtype=torch.float64, device="cuda"), Y)
+    torch.cuda.synchronize()
+    res["planted"]["spmm_column"] = [[{}, *split(pjds.pjds_check_word(clear=True))]]
     print(json.dumps(res))
 
 

@@ -38,7 +38,7 @@ def test_clean_runs_leave_the_check_word_at_zero(res):
 
 def test_planted_column_is_recorded_and_skipped(res):
     n = res["n"]
-    for cfg, code, idx in res["planted"]["column"] + res["planted"]["ellr_column"]:
+    for cfg, code, idx in res["planted"]["column"] + res["planted"]["ellr_column"] + res["planted"]["spmm_column"]:
         assert code == COLUMN and idx in (n["n_cols"] + 5, n["n_cols"] + 9), (cfg, code, idx)
     assert res["column_rows_changed"] == 1
 
