@@ -85,6 +85,10 @@ void pjds_abi_sizes(int32_t out[5]);
  * x gathers then share L2 sectors and their scattered y stores fill whole
  * sectors while the lines are still in L2. Each row's arithmetic does not
  * depend on the order.
+ * plan (n_plan entries of four int32) is not part of the format either: the
+ * per-tile mapping, the sorted rows cut into one-CTA tiles each mapped by its
+ * block's length (see pjds_dev). It assumes 16-byte aligned device arrays;
+ * the launcher checks.
  */
 typedef struct pjds_host {
   int32_t n_rows, n_cols, n_pad, b, n_blocks, n_max;
