@@ -6,6 +6,9 @@ Run on a GPU:
     python -m paper_1112_5588_gb300.tuner_data train timings.npz --model tuner_mlp.json
     python -m paper_1112_5588_gb300.tuner_data evaluate timings.npz --model tuner_mlp.json
     python -m paper_1112_5588_gb300.tuner_data recheck timings.npz --model tuner_mlp.json --count 200
+    python -m paper_1112_5588_gb300.tuner_data plan-eval timings.npz --rows train --out plan_train.npz
+    python -m paper_1112_5588_gb300.tuner_data plan-eval timings.npz --rows test --out plan_test.npz
+    python -m paper_1112_5588_gb300.tuner_data plan-fit plan_train.npz plan_test.npz      # CPU
 
 `generate` draws seeded synthetic matrices (N log-uniform, Zipf(s) row
 lengths with s uniform in [1.5, 3] and a cap drawn from {64, ..., 1024},
@@ -21,6 +24,13 @@ the first `--count` held-out matrices from their stored parameters, times
 the candidate space again with the library as it is now, and reports the
 model's regret on those fresh timings and their agreement with the stored
 ones (the model is not retrained).
+
+`plan-eval` times, for each matrix and precision, the stored timings' best
+uniform candidate and the per-tile mapping at the same b in one sweep (L2
+flushed), and records how far the uniform rule's own pick is from the best
+in the stored timings. `plan-fit` chooses, per precision, the row count from
+which the default takes the per-tile mapping (fitted on the training
+matrices, reported on the held-out ones).
 """
 from __future__ import annotations
 
@@ -162,6 +172,79 @@ def recheck(data: dict, m, count: int, reps: int = 3, log=sys.stderr) -> dict:
             "regret_on_fresh_timings": evaluate(fresh, m)}
 
 
+def uniform_threads(n_rows: int, nnz: int, n_max: int, dtype: str) -> int:
+    """Threads per row of pjds_spmv's uniform mapping (api.cu): the longest
+    row's chain against the product's stream time, ratio = n_max * 2^20 /
+    (nnz * entry bytes); 1 below 2, 2 below 8, 4 below 64, else 8; doubled
+    while n_rows * T < 2^17."""
+    entry = {"f64": 12, "f32": 8, "bf16": 6}[dtype]
+    num, den = n_max * 2**20, max(nnz, 1) * entry
+    t = 1 if num < 2 * den else 2 if num < 8 * den else 4 if num < 64 * den else 8
+    while t < 8 and n_rows * t < 2**17:
+        t *= 2
+    return t
+
+
+def plan_eval(data: dict, rows, reps: int = 3, log=sys.stderr) -> dict:
+    """Per matrix row i and precision: the re-timed best uniform candidate,
+    the per-tile mapping at its b (one sweep, L2 flushed), and the uniform
+    rule's stored time over the stored best."""
+    from . import tune
+    cands = json.loads(str(data["cands"]))
+    params = json.loads(str(data["params"]))
+    stored = data["times_us"]
+    ci = {(c["b"], c["dtype"], c["threads_per_row"]): k for k, c in enumerate(cands)}
+    out = {"i": [], "n": []}
+    for dt in DTYPES:
+        out[f"{dt}_uniform_us"], out[f"{dt}_plan_us"], out[f"{dt}_rule_over_best"] = [], [], []
+    t0 = time.time()
+    for k, i in enumerate(rows):
+        A = make_matrix(params[i])
+        lens = np.diff(A.row_ptr)
+        test = []
+        for dt in DTYPES:
+            idx = [c for c, cd in enumerate(cands) if cd["dtype"] == dt]
+            best = min(idx, key=lambda c: stored[i, c])
+            cand = {key: cands[best][key] for key in ("b", "dtype", "rows_per_thread", "threads_per_row",
+                                                      "block_threads", "unroll", "staged")}
+            test += [cand, {"b": cand["b"], "dtype": dt, "plan": 1}]
+        entries, _ = tune.sweep(A, test, reps=reps)
+        out["i"].append(i)
+        out["n"].append(A.n_rows)
+        for j, dt in enumerate(DTYPES):
+            u, p = entries[2 * j], entries[2 * j + 1]
+            ok = u["status"] == 0 and p["status"] == 0
+            t_rule = uniform_threads(A.n_rows, A.nnz, int(lens.max()), dt)
+            best_stored = np.nanmin([stored[i, c] for c, cd in enumerate(cands) if cd["dtype"] == dt])
+            out[f"{dt}_uniform_us"].append(u["us"] if ok else np.nan)
+            out[f"{dt}_plan_us"].append(p["us"] if ok else np.nan)
+            out[f"{dt}_rule_over_best"].append(stored[i, ci[(32, dt, t_rule)]] / best_stored)
+        if (k + 1) % 200 == 0:
+            print(f"[tuner_data] plan-eval {k + 1}/{len(rows)}, {time.time() - t0:.0f} s", file=log, flush=True)
+    return {key: np.asarray(v) for key, v in out.items()}
+
+
+def plan_fit(train: dict, test: dict) -> dict:
+    """Per precision, the power-of-two row count from which taking the
+    per-tile mapping (else the uniform rule) minimises the geometric mean of
+    the time over the best uniform candidate on the training matrices; that
+    mean on the held-out matrices, beside the uniform rule alone and the plan
+    always."""
+    def score(d, dt, thr):
+        u, p, r = d[f"{dt}_uniform_us"], d[f"{dt}_plan_us"], d[f"{dt}_rule_over_best"]
+        ok = np.isfinite(u) & np.isfinite(p) & np.isfinite(r)
+        t = np.where(d["n"] >= thr, p, u * r)
+        return float(np.exp(np.mean(np.log(t[ok] / u[ok]))))
+    res = {}
+    for dt in DTYPES:
+        cands = [2 ** k for k in range(14, 23)]
+        thr = min(cands, key=lambda t: score(train, dt, t))
+        res[dt] = {"min_rows": thr, "train": round(score(train, dt, thr), 3), "test": round(score(test, dt, thr), 3),
+                   "test_rule_only": round(score(test, dt, float("inf")), 3),
+                   "test_plan_always": round(score(test, dt, 0), 3)}
+    return res
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -185,6 +268,13 @@ def main(argv=None) -> int:
     r.add_argument("data")
     r.add_argument("--model", required=True)
     r.add_argument("--count", type=int, default=200)
+    pe = sub.add_parser("plan-eval")
+    pe.add_argument("data")
+    pe.add_argument("--rows", choices=["train", "test"], required=True)
+    pe.add_argument("--out", required=True)
+    pf = sub.add_parser("plan-fit")
+    pf.add_argument("train")
+    pf.add_argument("test")
     a = ap.parse_args(argv)
     if a.cmd == "generate":
         d = generate(a.n_train, a.n_test, a.seed, a.n_lo, a.n_hi)
@@ -199,6 +289,14 @@ def main(argv=None) -> int:
                                   "data": a.data, "heldout": ev})
         print(json.dumps({"model": a.model, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
                           "heldout": ev}))
+    elif a.cmd == "plan-eval":
+        d = dict(np.load(a.data, allow_pickle=False))
+        nt = int(d["n_train"])
+        rows = range(0, nt) if a.rows == "train" else range(nt, len(d["times_us"]))
+        np.savez_compressed(a.out, **plan_eval(d, rows))
+        print(json.dumps({"saved": a.out, "matrices": len(rows)}))
+    elif a.cmd == "plan-fit":
+        print(json.dumps(plan_fit(dict(np.load(a.train)), dict(np.load(a.test)))))
     elif a.cmd == "recheck":
         from . import learned
         d = dict(np.load(a.data, allow_pickle=False))
