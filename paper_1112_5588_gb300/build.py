@@ -5,7 +5,8 @@ g++ for .cpp, both with OpenMP for the host converter), then nvcc links the
 shared library with the static CUDA runtime. Objects go to csrc/_build/;
 unchanged sources are not recompiled.
 
-Run as ``python -m paper_1112_5588_gb300.build`` or call ``build()``.
+Run as ``python -m paper_1112_5588_gb300.build [--force] [--ptxas] [--checked]`` or call ``build()``;
+``--checked`` builds libpjds_checked.so (device-side extent checks, a test build).
 """
 from __future__ import annotations
 
@@ -88,4 +89,4 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="--ptxas" in sys.argv, checked="--checked" in sys.argv))
