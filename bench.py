@@ -150,6 +150,8 @@ def gpu_id_for_smi(torch, dev) -> str:
 
 
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "case":
+        return run_case(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -170,6 +172,22 @@ def main():
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local_rank)
+
+
+def synth_vector(n, seed):
+    import synth
+    return synth.vector(n, seed=seed)
+
+
+def kernel_name(cfg: dict) -> str:
+    """Readable name of the kernel pjds_spmv launches for a resolved config."""
+    if cfg.get("plan") == 1:
+        return "pjds_plan_kernel (per-tile mapping)"
+    order = "tile order" if cfg.get("tile_order") == 1 else "sorted order"
+    if cfg.get("threads_per_row", 1) > 1:
+        return f"pjds_tpr_kernel T={cfg['threads_per_row']} U={cfg['unroll']} {cfg['block_threads']} thr/CTA, {order}"
+    return (f"pjds_rows_kernel R={cfg['rows_per_thread']} U={cfg['unroll']} {cfg['block_threads']} thr/CTA, "
+            f"{order}")
 
 
 def workload_desc(n):
@@ -259,6 +277,7 @@ def run_ours(args, world, rank, local_rank):
     H.destroy()
     xt = torch.from_numpy(x).to(dev)
     y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+    y_pat = torch.empty_like(y)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     nbytes = alg_bytes(A.n_rows, A.n_cols, A.nnz, 8, 8)
 
@@ -274,13 +293,19 @@ def run_ours(args, world, rank, local_rank):
         barrier()
         torch.cuda.synchronize()
     gpu_launches = args.steps
+    # gather ceiling: the same traversal without the value stream (the
+    # pattern product y = S x), timed the same way right after the product
+    durs_pat = time_launches(torch, lambda: pjds.pjds_spmv_pattern(D, xt, y_pat), args.steps, args.warmup, flush)
     # replicas: units of all ranks over the slowest rank's time
     total_bytes, t_total, rate = replicas.aggregate(nbytes * args.steps, sum(durs), dev if dist_on else None)
     value = rate / 1e9
     per_launch = t_total / args.steps
     peak, peak_kind = hbm_peak()
     achieved = nbytes / (sum(durs) / len(durs)) / 1e9
+    t_pat = sum(durs_pat) / len(durs_pat)
+    ceiling_gbs = nbytes / t_pat / 1e9
     y_gpu = y.cpu().numpy()
+    y_pat_gpu = y_pat.cpu().numpy()
 
     side = {}
     prec_gpu = None
@@ -296,16 +321,27 @@ def run_ours(args, world, rank, local_rank):
     # products in one pjds_spmv_host_stream call (each step copies its x in
     # and its y out; the copies overlap the products), and K single
     # pjds_spmv_host calls (copy in, product, copy out, one after the other)
-    xh = torch.from_numpy(x).pin_memory()
-    yhs = [torch.empty(A.n_rows, dtype=torch.float64).pin_memory() for _ in range(2)]
+    # four different x vectors in turn, one host y per step; every step's y
+    # is compared with the device product of its x afterwards
+    n_x = 4
+    xhs = [torch.from_numpy(synth_vector(A.n_cols, args.seed + 100 + v)).pin_memory() for v in range(n_x)]
+    y_want = []
+    for xv in xhs:
+        pjds.pjds_spmv(D, xv.to(dev), y)
+        y_want.append(y.cpu().numpy().copy())
+    yhs = [torch.empty(A.n_rows, dtype=torch.float64).pin_memory() for _ in range(max(args.steps, args.warmup))]
     xd2 = [torch.empty_like(xt) for _ in range(2)]
     yd2 = [torch.empty_like(y) for _ in range(2)]
-    pjds.pjds_spmv_host_stream(D, [xh] * args.warmup, [yhs[v % 2] for v in range(args.warmup)], xd2, yd2)
+    pjds.pjds_spmv_host_stream(D, [xhs[v % n_x] for v in range(args.warmup)], yhs[:args.warmup], xd2, yd2)
+    for yh in yhs:
+        yh.fill_(float("nan"))
     barrier()
     t0 = time.perf_counter()
-    pjds.pjds_spmv_host_stream(D, [xh] * args.steps, [yhs[v % 2] for v in range(args.steps)], xd2, yd2)
+    pjds.pjds_spmv_host_stream(D, [xhs[v % n_x] for v in range(args.steps)], yhs[:args.steps], xd2, yd2)
     t_stream = time.perf_counter() - t0
-    e2e_check = bool(np.array_equal(yhs[(args.steps - 1) % 2].numpy(), y_gpu))
+    e2e_steps_ok = [bool(np.array_equal(yhs[v].numpy(), y_want[v % n_x])) for v in range(args.steps)]
+    e2e_check = all(e2e_steps_ok)
+    xh = xhs[0]
     _, _, e2e_rate = replicas.aggregate(nbytes * args.steps, t_stream, dev if dist_on else None)
     e2e_value = e2e_rate / 1e9
     for _ in range(args.warmup):
@@ -326,6 +362,7 @@ def run_ours(args, world, rank, local_rank):
     # ---------------- CPU baseline: the fp64 oracle on the host cores (rank 0, N = 1)
     cpu = None
     err = None
+    pattern_exact = None
     if world == 1:
         import oracle
         oracle.build()
@@ -353,9 +390,16 @@ def run_ours(args, world, rank, local_rank):
                            "gflops": round(2 * A.nnz * reps1 / t1 / 1e9, 3), "products": reps1}
         absax = oracle.crs_absmv(A, x)
         err = float(np.max(np.abs(y_gpu - y_ref)) / np.max(absax))
+        # the pattern product against the oracle's product with unit values
+        ones = type(A)(A.n_rows, A.n_cols, A.row_ptr, A.col, np.ones(A.nnz))
+        pattern_exact = bool(np.array_equal(y_pat_gpu, oracle.crs_spmv(ones, x)))
+        if side:
+            side["side"] = reduced_precision_oracle_checks(oracle, A, x, y_ref, absax, side["side"])
         if prec_gpu is not None:
             prec_gpu = precision_oracle_checks(oracle, prec_gpu)
 
+    if side:
+        side["side"].pop("_reduced_results", None)
     # the paper's model (Eqs. 1-2) with this GPU's measured bandwidths
     from paper_1112_5588_gb300 import perfmodel as pm
     n_nzr = A.nnz / A.n_rows
@@ -387,12 +431,19 @@ def run_ours(args, world, rank, local_rank):
         "gflops": round(value * 2 * A.nnz / nbytes, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "pjds_rows_kernel<double,double,int,R=1,U=4,scatter> 256 thr/CTA, tile order",
-                     "peak_kind": peak_kind},
+                     "kernel": kernel_name(launched),
+                     "peak_kind": peak_kind,
+                     "gather_ceiling_gbs": round(ceiling_gbs, 2),
+                     "gather_ceiling_us": round(t_pat * 1e6, 2),
+                     "frac_of_min_hbm_gather_ceiling": round(achieved / min(peak, ceiling_gbs), 4),
+                     "gather_ceiling_kernel": "pattern product (pjds_spmv_pattern): the same traversal, column "
+                                              "stream, x gathers and y stores, no value stream",
+                     "gather_ceiling_bitwise_equals_oracle": pattern_exact},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "GB/s", "h2d_bytes_per_step": 8 * A.n_cols,
                 "d2h_bytes_per_step": 8 * A.n_rows, "api": "pjds_spmv_host_stream (K products, copies overlapped)",
                 "result_equals_device_product": e2e_check,
+                "steps_checked": len(e2e_steps_ok), "distinct_x": n_x,
                 "single_call_value": round(e2e_single_rate / 1e9, 3),
                 "single_call_api": "pjds_spmv_host (copy in, product, copy out per call)"},
         "gpu_launches": gpu_launches,
@@ -437,6 +488,8 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
     out["pjds_data_reduction_vs_ellpack"] = round(1 - D.n_stored / ell_stored, 4)
     del ED, ye
 
+    peak = hbm_peak()[0]
+    reduced = {}
     for dt in ("f32", "bf16"):
         Hr = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dt)
         Dr = Hr.to_device(dev)
@@ -446,11 +499,26 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
         tr = med(time_launches(torch, lambda: pjds.pjds_spmv(Dr, xr, yr), K, W, flush))
         vb = 4 if dt == "f32" else 2
         b_r = alg_bytes(A.n_rows, A.n_cols, A.nnz, vb, 4)
-        dy = (yr.double() - y).abs().max().item()
         out[f"pjds_{dt}"] = {"gbs": round(b_r / tr / 1e9, 1), "gflops": round(2 * A.nnz / tr / 1e9, 2),
-                             "us": round(tr * 1e6, 2), "speedup_vs_f64": round(t_p / tr, 3),
-                             "max_abs_diff_vs_f64_gpu": dy}
+                             "us": round(tr * 1e6, 2), "frac_of_hbm": round(b_r / tr / 1e9 / peak, 4),
+                             "alg_bytes": b_r, "speedup_vs_f64": round(t_p / tr, 3),
+                             "kernel": kernel_name(pjds.pjds_spmv_resolve(Dr))}
+        reduced[f"pjds_{dt}"] = (dt, yr.cpu().numpy().copy())
         del Dr, xr, yr
+    # ELLPACK-R with fp32 values on the same matrix (Table 1's single-precision row)
+    E32 = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype="f32")
+    ED32 = E32.to_device(dev)
+    E32.destroy()
+    x32 = xt.float()
+    y32 = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
+    t_e32 = med(time_launches(torch, lambda: pjds.ellr_spmv(ED32, x32, y32), K, W, flush))
+    b_e32 = alg_bytes(A.n_rows, A.n_cols, A.nnz, 4, 4, scatter=False) + 4 * A.n_rows
+    out["ellr_f32"] = {"gbs": round(b_e32 / t_e32 / 1e9, 1), "gflops": round(2 * A.nnz / t_e32 / 1e9, 2),
+                       "us": round(t_e32 * 1e6, 2), "frac_of_hbm": round(b_e32 / t_e32 / 1e9 / peak, 4),
+                       "pjds_f32_vs_ellr_f32_speed": round(t_e32 * 1e6 / out["pjds_f32"]["us"], 3)}
+    reduced["ellr_f32"] = ("f32", y32.cpu().numpy().copy())
+    del ED32, x32, y32
+    out["_reduced_results"] = reduced
 
     Hp = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64", permute_cols=True)
     Dp = Hp.to_device(dev)
@@ -789,6 +857,27 @@ def spread_leg(torch, pjds, args, dev, flush):
     return out
 
 
+def reduced_precision_oracle_checks(oracle, A, x, y_ref, absax, side):
+    """Errors of the fp32 / bf16 products against the fp64 oracle: normwise
+    against the exact (fp64) matrix, and element by element against the
+    oracle's product of the rounded values the kernel holds, within the
+    fp32-accumulation bound of the parity tests."""
+    from tests import parity
+    reduced = side.pop("_reduced_results", {})
+    lens = np.diff(A.row_ptr)
+    x32 = x.astype(np.float32).astype(np.float64)
+    for key, (dt, yv) in reduced.items():
+        vals = oracle.round_f32(A.val) if dt == "f32" else oracle.round_bf16(A.val)
+        Ar = type(A)(A.n_rows, A.n_cols, A.row_ptr, A.col, vals)
+        y_r = oracle.crs_spmv(Ar, x32)
+        r = parity.check_fp32(yv, y_r, oracle.crs_absmv(Ar, x32), lens)
+        side[key]["error_vs_fp64_oracle"] = {
+            "normwise_vs_exact_matrix": float(np.max(np.abs(yv - y_ref)) / np.max(absax)),
+            "normwise_vs_rounded_matrix": r["normwise"],
+            "elementwise_bound_vs_rounded_matrix_ok": r["ok"], "elements_outside_bound": r["n_bad"]}
+    return side
+
+
 def precision_oracle_checks(oracle, pg):
     """CPU leg: fp64 oracle residuals of the GPU solutions and Ritz pairs."""
     S, b, rep = pg["S"], pg["b"], pg["report"]
@@ -803,6 +892,186 @@ def precision_oracle_checks(oracle, pg):
         L["rel_residual_oracle"] = float(np.linalg.norm(Ay - rq * y) / np.linalg.norm(y) / abs(rq))
     pg["report"] = rep
     return pg
+
+
+CASE_DOC = """Run one pJDS product case a few times, for profiling under ncu.
+
+    python bench.py case --matrix stencil --g 100 --dtype f64 --permuted --staged --reps 3
+
+Builds one seeded synthetic matrix, converts it, uploads it and launches the
+chosen product `--reps` times (after `--warmup` launches) on the current
+stream, then prints one JSON line with the CUDA-event time of each launch.
+Matrices: hmep (--n rows), stencil (--g grid), dlr (--n rows, 144/row), zipf
+(--n rows). Kinds: spmv (default), pattern (the pattern product), ellr, spmm (--k right-hand sides);
+cg (one mixed-precision CG solve of `--reps` inner steps in the permuted
+basis, fp64 outer matrix, --dtype inner matrix, no graph) and lanczos
+(`--reps` steps, no graph) on the stencil; batch (--mats Zipf matrices with
+N log-uniform in [10k, --n], one persistent launch per repetition); mlp (the
+learned tuner's cost model trained for `--reps` epochs on the committed
+timing data, then inference over the candidates of the held-out matrices).
+"""
+
+
+def run_case(argv) -> int:
+    ap = argparse.ArgumentParser(prog="bench.py case", description=CASE_DOC)
+    ap.add_argument("--matrix", choices=["hmep", "stencil", "dlr", "zipf"], default="hmep")
+    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--g", type=int, default=100)
+    ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
+    ap.add_argument("--kind", choices=["spmv", "pattern", "ellr", "spmm", "cg", "lanczos", "batch", "mlp"],
+                    default="spmv")
+    ap.add_argument("--mats", type=int, default=64)
+    ap.add_argument("--k", type=int, default=8)
+    ap.add_argument("--permuted", action="store_true")
+    ap.add_argument("--staged", action="store_true")
+    ap.add_argument("--threads-per-row", type=int, default=0)
+    ap.add_argument("--rows-per-thread", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=1234)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    import synth
+    from paper_1112_5588_gb300 import batch, krylov, pjds
+
+    dev = torch.device("cuda")
+    if a.kind == "mlp":
+        return run_mlp(a, torch)
+    if a.kind == "batch":
+        return run_batch(a, torch, synth, batch, pjds, dev)
+    if a.kind in ("cg", "lanczos"):
+        return run_krylov(a, torch, synth, krylov, pjds, dev)
+    if a.matrix == "hmep":
+        A = synth.hmep_like(n=a.n, seed=a.seed)
+    elif a.matrix == "stencil":
+        A = synth.stencil27(g=a.g, seed=a.seed)
+    elif a.matrix == "dlr":
+        A = synth.block_dense(n_brow=max(1, a.n // 4), bs=4, nb=36, frac=0.05, seed=a.seed)
+    else:
+        A = synth.zipf_rows(a.n, s=2.0, len_max=512, seed=a.seed)
+    if a.kind == "ellr":
+        D = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype=a.dtype).to_device(dev)
+    else:
+        D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=a.dtype,
+                             permute_cols=a.permuted).to_device(dev)
+    if a.kind == "spmm":
+        X = torch.rand(A.n_cols, a.k, device=dev, dtype=D.vec_dtype)
+        Y = torch.empty(A.n_rows, a.k, device=dev, dtype=D.vec_dtype)
+        run = lambda: batch.spmm(D, X, Y)  # noqa: E731
+    else:
+        x = torch.from_numpy(synth.vector(A.n_cols, seed=a.seed)).to(dev, D.vec_dtype)
+        y = torch.empty(A.n_rows, device=dev, dtype=D.vec_dtype)
+        if a.kind == "ellr":
+            run = lambda: pjds.ellr_spmv(D, x, y)  # noqa: E731
+        else:
+            kw = dict(staged=1 if a.staged else 0, threads_per_row=a.threads_per_row,
+                      rows_per_thread=a.rows_per_thread)
+            run = (lambda: pjds.pjds_spmv_pattern(D, x, y, **kw)) if a.kind == "pattern" else (  # noqa: E731
+                lambda: pjds.pjds_spmv_cfg(D, x, y, **kw))
+    for _ in range(a.warmup):
+        run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    status = pjds.pjds_device_status() if a.staged else 0
+    print(json.dumps({"matrix": a.matrix, "n_rows": A.n_rows, "nnz": A.nnz, "dtype": a.dtype, "kind": a.kind,
+                      "permuted": a.permuted, "staged": a.staged, "us": [round(t, 2) for t in times],
+                      "device_status": status}))
+    return 0 if status == 0 else 1
+
+
+def _timed(torch, run, reps, warmup):
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(round(e0.elapsed_time(e1) * 1e3, 2))
+    return times
+
+
+def run_mlp(a, torch) -> int:
+    import os
+    import time
+    from paper_1112_5588_gb300 import learned, tuner_data
+    data = dict(np.load(os.path.join(ROOT, "paper_1112_5588_gb300", "data", "tuner_timings_gb300.npz"),
+                        allow_pickle=False))
+    X, y = tuner_data.samples(data, range(int(data["n_train"])))
+    m = learned.init(1)
+    learned.fit_scaling(m, X, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = learned.train(m, X, y, epochs=a.reps, batch=1024, lr=2e-3, seed=1)
+    t_train = time.perf_counter() - t0
+    cands = __import__("json").loads(str(data["cands"]))
+    rows = range(int(data["n_train"]), len(data["times_us"]))
+    enc = np.concatenate([learned.encode(data["features"][i], cands) for i in rows])
+    learned.predict(m, enc)
+    t0 = time.perf_counter()
+    learned.predict(m, enc)
+    t_pred = time.perf_counter() - t0
+    print(json.dumps({"kind": "mlp", "samples": int(len(y)), "epochs": a.reps, "train_s": round(t_train, 3),
+                      "s_per_epoch": round(t_train / max(a.reps, 1), 4), "loss_first": float(hist[0]),
+                      "loss_last": float(hist[-1]), "predict_rows": int(len(enc)), "predict_us": round(t_pred * 1e6, 1)}))
+    return 0
+
+
+def run_batch(a, torch, synth, batch, pjds, dev) -> int:
+    rng = np.random.default_rng(a.seed)
+    sizes = np.exp(rng.uniform(np.log(10_000), np.log(max(a.n, 10_001)), a.mats)).astype(int)
+    devs, xs, ys, nnz = [], [], [], 0
+    for m, n in enumerate(sizes):
+        M = synth.zipf_rows(int(n), s=2.0, len_max=512, seed=a.seed + m)
+        nnz += M.nnz
+        devs.append(pjds.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32,
+                                     dtype=a.dtype).to_device(dev))
+        xs.append(torch.from_numpy(synth.vector(M.n_cols, seed=m)).to(dev, devs[-1].vec_dtype))
+        ys.append(torch.empty(M.n_rows, dtype=devs[-1].vec_dtype, device=dev))
+    B = batch.Batch(devs, xs, ys)
+    times = _timed(torch, lambda: B.run(use_graph=False), a.reps, a.warmup)
+    info = B.info()
+    B.destroy()
+    print(json.dumps({"kind": "batch", "n_mats": a.mats, "total_rows": int(sizes.sum()), "nnz": int(nnz),
+                      "dtype": a.dtype, **info, "us": times}))
+    return 0
+
+
+def run_krylov(a, torch, synth, krylov, pjds, dev) -> int:
+    A = synth.stencil27(g=a.g, seed=a.seed)
+    H64 = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64", permute_cols=True)
+    D64 = H64.to_device(dev)
+    H64.destroy()
+    if a.kind == "cg":
+        Dlo = D64 if a.dtype == "f64" else pjds.pjds_create(
+            A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=a.dtype, permute_cols=True).to_device(dev)
+        b = torch.from_numpy(synth.vector(A.n_rows, seed=a.seed)).to(dev)
+        x = torch.zeros_like(b)
+
+        def run():
+            x.zero_()
+            krylov.cg_solve(D64, Dlo, b, x, max_outer=1, inner_iters=a.reps, use_graph=False)
+        times = _timed(torch, run, 1, a.warmup)
+    else:
+        D = D64 if a.dtype == "f64" else pjds.pjds_create(
+            A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=a.dtype, permute_cols=True).to_device(dev)
+        v0 = torch.from_numpy(synth.vector(A.n_rows, seed=a.seed)).to(dev, D.vec_dtype)
+        times = _timed(torch, lambda: krylov.lanczos(D, v0, a.reps, use_graph=False), 1, a.warmup)
+    print(json.dumps({"kind": a.kind, "matrix": f"stencil g={a.g}", "n_rows": A.n_rows, "nnz": A.nnz,
+                      "dtype": a.dtype, "steps": a.reps, "us_total": times}))
+    return 0
 
 
 if __name__ == "__main__":

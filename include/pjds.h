@@ -166,6 +166,10 @@ int pjds_destroy(pjds_host *h);
  * fused multiply-add, then
  *   - permute_cols = 0: writes y[perm[i]] (x and y in the original basis);
  *   - permute_cols = 1: writes y[i] (x and y in the permuted basis).
+ * The basis is a property of the matrix handle, fixed by pjds_create's
+ * permute_cols, not an argument of the call: in the permuted basis the column
+ * indices themselves are renumbered, so one set of device arrays serves one
+ * basis only (create the matrix twice to use both).
  * x: n_cols elements, y: n_rows elements, device memory of the vector type of
  * A->dtype; x and y must not overlap. Every element of y is written.
  * Mapping (the default of pjds_spmv_cfg): the per-tile mapping of A->plan
@@ -258,6 +262,22 @@ int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *
  * pjds_spmv_cfg rejects.
  */
 int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *out);
+
+/*
+ * Pattern product y = S x, S the sparsity pattern of A (every stored entry
+ * taken as 1): sorted row i sums x[col[col_start[j] + i]] for j < len(i), in
+ * order, with plain additions, and writes y[perm[i]] (y[i] in the permuted
+ * basis). It runs the traversal pjds_spmv_cfg would run for cfg (NULL: the
+ * pjds_spmv default) without reading val: the column stream, the x gathers
+ * and the y stores of the product and nothing else. Its time is therefore a
+ * floor for the product's time with the same traversal, the gather ceiling
+ * against which the product is measured besides HBM bandwidth (Eq. 1: the
+ * alpha term, the traffic the right-hand side costs, is this part). One
+ * thread per row only: a configuration that resolves to the per-tile plan,
+ * the staged kernel, several rows or several threads per row returns
+ * PJDS_EINVAL. The paper has no counterpart of this call.
+ */
+int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
 
 /*
  * Device status word of the staged kernel (see pjds_launch.staged): 0 when

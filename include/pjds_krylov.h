@@ -89,9 +89,14 @@ int pjds_cg_solve(const pjds_dev *A_hi, const pjds_dev *A_lo, const double *b, d
  *   - at most 131072 rows; larger matrices return PJDS_EINVAL (use
  *     pjds_cg_solve with a caller workspace);
  *   - the first call on a device (with that device current) looks up the
- *     array's device address once; make that first call before any stream
- *     capture;
- *   - no cudaMalloc, cudaFree or allocating library call is made;
+ *     array's device address once and keeps it for the life of the process;
+ *     make that first call before any stream capture, and do not use the
+ *     library across cudaDeviceReset (the kept address would then be stale);
+ *   - opts->use_graph is ignored: the inner steps are launched one by one on
+ *     `stream`, so the call creates no stream, graph or other driver object;
+ *   - no cudaMalloc, cudaFree or allocating library call is made (the call
+ *     issues kernels, one cudaMemsetAsync on the array and a small
+ *     device-to-host copy of the residual norm per outer step);
  *   - all calls share the one array per device and it keeps the previous
  *     call's contents: each call clears the scalar block it reads and writes
  *     every vector before reading it, but calls that overlap on the GPU

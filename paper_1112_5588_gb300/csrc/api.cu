@@ -190,6 +190,19 @@ extern "C" int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pj
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream) {
+  clear_error();
+  int rc = check_pjds_dev(A, x, y);
+  if (rc) return rc;
+  LaunchCfg c;
+  rc = resolve_cfg(A, cfg, c);
+  if (rc) return rc;
+  if (c.plan || c.staged || c.rows_per_thread != 1 || c.threads_per_row != 1)
+    return set_error(PJDS_EINVAL, "the pattern product runs the one-thread-per-row mappings only");
+  c.pattern = 1;
+  return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int pjds_device_status(int32_t *status, int32_t clear, void *stream) {
   clear_error();
   if (!status) return set_error(PJDS_EINVAL, "status is NULL");

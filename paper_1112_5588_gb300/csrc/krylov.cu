@@ -1010,7 +1010,10 @@ static void *g_cg_static_ptr[kMaxDevices];
 static std::mutex g_cg_static_mu;
 
 // Device address of the static workspace on the current device (set up on
-// the first call per device).
+// the first call per device). The address is kept for the life of the
+// process: after cudaDeviceReset the module is loaded again and the kept
+// address no longer names the array, so the library must not be used across
+// a reset of the device.
 static int cg_static_workspace(void **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1053,6 +1056,10 @@ extern "C" int pjds_cg_solve_static(const pjds_dev *A_hi, const pjds_dev *A_lo, 
     if (o.inner_iters <= 0) o.inner_iters = 50;
   }
   if (o.inner_iters > 100000 || o.max_outer > 100000) return set_error(PJDS_EINVAL, "iteration counts too large");
+  // The inner steps are always launched one by one on the caller's stream:
+  // recording them into a CUDA graph would create a stream and an executable
+  // graph, driver objects this entry point promises not to create.
+  o.use_graph = 0;
   const bool low = A_lo->dtype != PJDS_F64;
   const size_t need = cg_bytes(A_hi->n_rows, low ? 4 : 8);
   if (need > CG_STATIC_BYTES)

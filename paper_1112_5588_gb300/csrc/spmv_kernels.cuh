@@ -219,7 +219,9 @@ __device__ __forceinline__ TX gather_n(const TX *__restrict__ x, int32_t c, int3
 // 32 >= R). Loop bound: the block's padded length; pads are skipped. The
 // j-loop runs in chunks of U jagged diagonals; a chunk's loads are predicated
 // on j < L, so a short row issues all of its loads in ceil(L/U) rounds.
-template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER>
+// PAT: the pattern product (every stored value taken as 1, val not read):
+// the same column stream, x gathers and y stores, plain additions.
+template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER, bool PAT = false>
 __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
                                                         const int64_t *__restrict__ col_start,
                                                         const int32_t *__restrict__ block_len,
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
       }
       if (live) {
         ld_stream<R>(col + o, c[u]);
-        ld_stream<R>(val + o, v[u]);
+        if constexpr (!PAT) ld_stream<R>(val + o, v[u]);
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -267,8 +269,12 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        acc[r] = c[u][r] >= 0 ? fma_acc(to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
+      for (int r = 0; r < R; ++r) {
+        if constexpr (PAT)
+          acc[r] = c[u][r] >= 0 ? acc[r] + (TA)xv[u][r] : acc[r];
+        else
+          acc[r] = c[u][r] >= 0 ? fma_acc(to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
+      }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {

@@ -22,6 +22,7 @@ struct LaunchCfg {
   int index64;          // 1: 64-bit element offsets regardless of size
   int tile_order;       // 1: tiles taken in A->tile_order
   int plan;             // 1: per-tile mapping of A->plan (the fields above do not apply)
+  int pattern = 0;      // 1: the pattern product (values taken as 1, val not read)
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -66,8 +67,15 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
 #define PJDS_ARGS val, A->col, A->col_start, A->block_len, A->perm, order, x, y, A->n_rows, A->n_pad, A->b
   const int U = c.unroll;
 #define PJDS_ROWS(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
+#define PJDS_PAT(UU) dev::pjds_rows_kernel<TV, TX, IDX, 1, UU, SC, true><<<g, blk, 0, s>>>(PJDS_ARGS)
 #define PJDS_TPR(TT, UU) dev::pjds_tpr_kernel<TV, TX, IDX, TT, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
-  if (T == 1 && R == 1) {
+  if (c.pattern) {
+    if (T != 1 || R != 1) return set_error(PJDS_EINVAL, "the pattern product runs one thread per row");
+    if (U == 4) PJDS_PAT(4);
+    else if (U == 8) PJDS_PAT(8);
+    else if (U == 16) PJDS_PAT(16);
+    else return set_error(PJDS_EINVAL, "unroll must be 4, 8 or 16 for one row per thread");
+  } else if (T == 1 && R == 1) {
     if (U == 4) PJDS_ROWS(1, 4);
     else if (U == 8) PJDS_ROWS(1, 8);
     else if (U == 16) PJDS_ROWS(1, 16);
@@ -93,6 +101,7 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
     }
   }
 #undef PJDS_ROWS
+#undef PJDS_PAT
 #undef PJDS_TPR
 #undef PJDS_ARGS
   return check_launch("pjds_spmv launch");

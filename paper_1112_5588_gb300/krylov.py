@@ -77,13 +77,14 @@ def cg_solve(A_hi, A_lo, b: torch.Tensor, x: torch.Tensor, max_outer: int = 6, i
 
 
 def cg_solve_static(A_hi, A_lo, b: torch.Tensor, x: torch.Tensor, max_outer: int = 6, inner_iters: int = 50,
-                    tol: float = 0.0, use_graph: bool = True, stream=None) -> dict:
+                    tol: float = 0.0, stream=None) -> dict:
     """pjds_cg_solve_static: the same solve as cg_solve, for callers that
     cannot allocate device memory; the library's static device workspace
-    (at most 131072 rows) is used instead of a caller workspace."""
+    (at most 131072 rows) is used instead of a caller workspace, and the
+    inner steps are launched one by one (no CUDA graph is created)."""
     for t, nm in ((b, "b"), (x, "x")):
         _p._check_vec(t, A_hi.n_rows, torch.float64, nm)
-    o = _CgOpts(max_outer, inner_iters, tol, 1 if use_graph else 0, 0)
+    o = _CgOpts(max_outer, inner_iters, tol, 0, 0)
     r = _CgResult()
     _p._check(_lib.pjds_cg_solve_static(ctypes.byref(A_hi.struct),
                                         ctypes.byref(A_lo.struct) if A_lo is not None else None, b.data_ptr(),

@@ -84,6 +84,7 @@ def _load_lib():
         "pjds_destroy": (ctypes.c_int, [P(_PjdsHostS)]),
         "pjds_spmv": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_spmv_cfg": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, P(_LaunchS), _vp]),
+        "pjds_spmv_pattern": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, P(_LaunchS), _vp]),
         "pjds_spmv_host": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp, _vp, _vp]),
         "pjds_spmv_host_stream": (ctypes.c_int, [P(_PjdsDevS), _i32, P(_vp), P(_vp), P(_vp), P(_vp), _vp]),
         "pjds_spmv_resolve": (ctypes.c_int, [P(_PjdsDevS), P(_LaunchS), P(_LaunchS)]),
@@ -287,6 +288,21 @@ def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thre
     cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
+    return y
+
+
+def pjds_spmv_pattern(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None, **cfg) -> torch.Tensor:
+    """y = S x, S the sparsity pattern of A (values taken as 1; pjds_spmv_pattern):
+    the traversal of pjds_spmv_cfg(**cfg) without the value stream."""
+    _check_vec(x, A.n_cols, A.vec_dtype, "x")
+    _check_vec(y, A.n_rows, A.vec_dtype, "y")
+    keys = ("rows_per_thread", "threads_per_row", "block_threads", "unroll", "staged", "index64", "tile_order",
+            "plan")
+    c = _LaunchS(*[int(cfg.pop(k, 0)) for k in keys])
+    if cfg:
+        raise TypeError(f"unknown launch fields {sorted(cfg)}")
+    _check(_lib.pjds_spmv_pattern(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(c),
+                                  _stream_ptr(stream)), "pjds_spmv_pattern")
     return y
 
 

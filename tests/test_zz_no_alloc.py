@@ -45,13 +45,22 @@ def test_static_workspace_matches_caller_workspace_twice(mods, oracle_lib, lo):
         x_ref = torch.zeros_like(bp)
         x_st = torch.zeros_like(bp)
         ref = krylov.cg_solve(D64, Dlo, bp, x_ref, max_outer=6, inner_iters=50)
+        # use_graph = 1 is passed on purpose: the entry point ignores it and
+        # launches the inner steps directly, creating no graph
         o = krylov._CgOpts(6, 50, 0.0, 1, 0)
         r = krylov._CgResult()
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = lib.pjds_cg_solve_static(ctypes.byref(D64.struct), ctypes.byref(Dlo.struct) if Dlo else None,
                                       bp.data_ptr(), x_st.data_ptr(), ctypes.byref(o), ctypes.byref(r),
                                       torch.cuda.current_stream().cuda_stream)
         assert rc == 0, pjds.lib().pjds_last_error()
         torch.cuda.synchronize()
+        # nothing was allocated on the device by the second call (the first
+        # may still load the module that holds the array, where the driver
+        # loads modules lazily)
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before
         xs, xr = x_st.cpu().numpy(), x_ref.cpu().numpy()
         # tolerance of the CG tests: x within 1e-11 (relative, max norm), fp64 residual <= 1e-12
         assert np.max(np.abs(xs - xr)) <= 1e-11 * np.max(np.abs(xr)), call
