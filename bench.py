@@ -531,8 +531,9 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
     out["pjds_f64_permuted_basis"] = {"gbs": round(b_pm / t_pm / 1e9, 1), "us": round(t_pm * 1e6, 2)}
     del Dp, xp, yp
 
-    for cfg in ({"rows_per_thread": 2}, {"rows_per_thread": 4}, {"threads_per_row": 2}, {"block_threads": 512},
-                {"block_threads": 128}, {"staged": 1}, {"tile_order": -1}):
+    for cfg in ({"window": -1}, {"rows_per_thread": 2}, {"rows_per_thread": 4}, {"threads_per_row": 2},
+                {"block_threads": 512}, {"block_threads": 128}, {"staged": 1}, {"tile_order": -1},
+                {"window": 1, "unroll": 8}):
         tc = med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xt, y, **cfg), K, W, flush))
         key = "cfg_" + "_".join(f"{k}{v}" for k, v in cfg.items())
         out[key] = {"gbs": round(nbytes / tc / 1e9, 1), "us": round(tc * 1e6, 2)}
@@ -926,6 +927,11 @@ def run_case(argv) -> int:
     ap.add_argument("--staged", action="store_true")
     ap.add_argument("--threads-per-row", type=int, default=0)
     ap.add_argument("--rows-per-thread", type=int, default=0)
+    ap.add_argument("--window", type=int, default=0, help="0 automatic, 1 the window mapping, -1 not")
+    ap.add_argument("--tile-order", type=int, default=0)
+    ap.add_argument("--plan", type=int, default=0)
+    ap.add_argument("--unroll", type=int, default=0)
+    ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=1234)
@@ -967,7 +973,8 @@ def run_case(argv) -> int:
             run = lambda: pjds.ellr_spmv(D, x, y)  # noqa: E731
         else:
             kw = dict(staged=1 if a.staged else 0, threads_per_row=a.threads_per_row,
-                      rows_per_thread=a.rows_per_thread)
+                      rows_per_thread=a.rows_per_thread, window=a.window, tile_order=a.tile_order, plan=a.plan,
+                      unroll=a.unroll, block_threads=a.block_threads)
             run = (lambda: pjds.pjds_spmv_pattern(D, x, y, **kw)) if a.kind == "pattern" else (  # noqa: E731
                 lambda: pjds.pjds_spmv_cfg(D, x, y, **kw))
     for _ in range(a.warmup):
@@ -984,6 +991,7 @@ def run_case(argv) -> int:
     status = pjds.pjds_device_status() if a.staged else 0
     print(json.dumps({"matrix": a.matrix, "n_rows": A.n_rows, "nnz": A.nnz, "dtype": a.dtype, "kind": a.kind,
                       "permuted": a.permuted, "staged": a.staged, "us": [round(t, 2) for t in times],
+                      "cfg": pjds.pjds_spmv_resolve(D, **kw) if a.kind in ("spmv", "pattern") else None,
                       "device_status": status}))
     return 0 if status == 0 else 1
 

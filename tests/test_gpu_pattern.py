@@ -38,8 +38,11 @@ SHAPES = [
     ("zipf", lambda: synth.zipf_rows(60_000, s=2.0, len_max=512, seed=8)),
     ("single", lambda: tiny.from_lengths([3], 5, seed=2)),
 ]
-CFGS = [dict(plan=-1), dict(plan=-1, tile_order=-1), dict(plan=-1, tile_order=1), dict(plan=-1, unroll=8),
-        dict(plan=-1, unroll=16, block_threads=128), dict(plan=-1, index64=1)]
+# one thread per row (the pattern product's mappings); small matrices would
+# otherwise default to several threads per row
+CFGS = [dict(threads_per_row=1), dict(threads_per_row=1, tile_order=-1), dict(threads_per_row=1, tile_order=1),
+        dict(threads_per_row=1, unroll=8), dict(threads_per_row=1, unroll=16, block_threads=128),
+        dict(threads_per_row=1, index64=1)]
 
 
 @pytest.mark.parametrize("cfg", CFGS, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
@@ -64,7 +67,7 @@ def test_pattern_fp32_vectors_within_bound(P, oracle_lib, dtype):
     x = synth.vector(A.n_cols, seed=22).astype(np.float32)
     D = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype).to_device("cuda")
     y = torch.full((A.n_rows,), float("nan"), dtype=torch.float32, device="cuda")
-    P.pjds_spmv_pattern(D, torch.from_numpy(x).cuda(), y, plan=-1)
+    P.pjds_spmv_pattern(D, torch.from_numpy(x).cuda(), y, threads_per_row=1)
     torch.cuda.synchronize()
     S = _ones(A)
     xd = x.astype(np.float64)
@@ -81,7 +84,7 @@ def test_pattern_permuted_basis(P, oracle_lib):
     D = H.to_device("cuda")
     x = synth.vector(A.n_cols, seed=23)
     y = torch.full((A.n_rows,), float("nan"), dtype=torch.float64, device="cuda")
-    P.pjds_spmv_pattern(D, torch.from_numpy(x[perm]).cuda(), y, plan=-1)
+    P.pjds_spmv_pattern(D, torch.from_numpy(x[perm]).cuda(), y, threads_per_row=1)
     torch.cuda.synchronize()
     want = oracle_lib.crs_spmv(_ones(A), x)[perm]
     assert np.array_equal(y.cpu().numpy().view(np.uint64), want.view(np.uint64))
