@@ -53,8 +53,8 @@ static int dispatch_pjds(const pjds_dev *A, const void *x, void *y, const Launch
 static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   if (c.window) {
     if (c.staged || c.plan) return set_error(PJDS_EINVAL, "the window mapping excludes staged and plan = 1");
-    if (c.rows_per_thread != 1 || c.threads_per_row != 1)
-      return set_error(PJDS_EINVAL, "the window mapping runs one thread per row");
+    if ((c.rows_per_thread != 1 && c.rows_per_thread != 2) || c.threads_per_row != 1)
+      return set_error(PJDS_EINVAL, "the window mapping runs one thread per row, one or two rows per thread");
     if (!window_usable(A))
       return set_error(PJDS_EINVAL, "window = 1 needs A's window plan, its tile_order and the original basis");
     if (c.unroll == 0) c.unroll = A->dtype == PJDS_F32 ? 8 : 4;
@@ -187,11 +187,11 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->window == 1) {
       if (cfg->plan == 1) return set_error(PJDS_EINVAL, "plan = 1 and window = 1 are exclusive");
       if (cfg->staged) return set_error(PJDS_EINVAL, "staged and window = 1 are exclusive");
-      if (cfg->rows_per_thread > 1 || cfg->threads_per_row > 1)
-        return set_error(PJDS_EINVAL, "the window mapping runs one thread per row");
+      if (cfg->rows_per_thread > 2 || cfg->threads_per_row > 1)
+        return set_error(PJDS_EINVAL, "the window mapping runs one thread per row, one or two rows per thread");
       c.window = 1;
       c.plan = 0;
-      c.rows_per_thread = 1;
+      c.rows_per_thread = cfg->rows_per_thread == 2 ? 2 : 1;
       c.threads_per_row = 1;
     } else if (cfg->window == -1 || cfg->plan || cfg->rows_per_thread || cfg->threads_per_row ||
                cfg->block_threads || cfg->staged || cfg->tile_order) {
@@ -255,7 +255,7 @@ extern "C" int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, cons
   LaunchCfg c;
   rc = resolve_cfg(A, cfg, c);
   if (rc) return rc;
-  if (c.plan || c.staged || c.rows_per_thread != 1 || c.threads_per_row != 1)
+  if (c.plan || c.staged || c.threads_per_row != 1 || (c.rows_per_thread != 1 && !c.window))
     return set_error(PJDS_EINVAL, "the pattern product runs the one-thread-per-row mappings only (uniform or window)");
   c.pattern = 1;
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));

@@ -114,9 +114,9 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
 }
 
 // Window mapping: one CTA per window of A->win_rows original rows (window.cuh).
-template <typename TV, typename TX, typename IDX, int U, bool PAT>
+template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT>
 int launch_window_u(const win::Desc &d, size_t smem, int32_t n_win, cudaStream_t s) {
-  auto kern = win::pjds_window_kernel<TV, TX, IDX, U, PAT>;
+  auto kern = win::pjds_window_kernel<TV, TX, IDX, U, RT, PAT>;
   // the dynamic shared-memory limit is raised once per device (the kernel's
   // requirement is at most the plan's budget)
   static int raised[64] = {0};
@@ -166,11 +166,19 @@ int launch_window(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cud
   d.reserved = 0;
   const size_t smem = ((size_t)off + (size_t)d.W) * sizeof(TX) + ((size_t)d.W + 31) / 32 * 4;
   if (smem > 160 * 1024) return set_error(PJDS_EINVAL, "window plan needs %zu bytes of shared memory", smem);
-  if (c.pattern)
-    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, true>(d, smem, A->n_win, s)
-                         : launch_window_u<TV, TX, IDX, 4, true>(d, smem, A->n_win, s);
-  return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, false>(d, smem, A->n_win, s)
-                       : launch_window_u<TV, TX, IDX, 4, false>(d, smem, A->n_win, s);
+  const bool two = c.rows_per_thread == 2;
+  if (c.pattern) {
+    if (two)
+      return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, true>(d, smem, A->n_win, s)
+                           : launch_window_u<TV, TX, IDX, 4, 2, true>(d, smem, A->n_win, s);
+    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, true>(d, smem, A->n_win, s)
+                         : launch_window_u<TV, TX, IDX, 4, 1, true>(d, smem, A->n_win, s);
+  }
+  if (two)
+    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, false>(d, smem, A->n_win, s)
+                         : launch_window_u<TV, TX, IDX, 4, 2, false>(d, smem, A->n_win, s);
+  return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, false>(d, smem, A->n_win, s)
+                       : launch_window_u<TV, TX, IDX, 4, 1, false>(d, smem, A->n_win, s);
 }
 
 // Per-tile mapping: one CTA per plan entry (tiles.cuh).

@@ -55,7 +55,46 @@ __device__ __forceinline__ TX gather_win(const Desc &d, const TX *sx, const TX *
   return PJDS_IN(c, d.n_cols, dev::CHK_COLUMN) ? __ldg(x + c) : TX(0);
 }
 
+// One row's partial sum over jagged diagonals [j, j + U) (loads predicated on
+// j + u < L; pads carry column -1 and add nothing).
 template <typename TV, typename TX, typename IDX, int U, bool PAT>
+__device__ __forceinline__ void row_chunk(const Desc &d, const TV *__restrict__ val, const TX *sx,
+                                          const TX *__restrict__ x, int64_t i, int32_t L, int32_t j, int32_t a,
+                                          typename dev::Acc<TV>::T &acc) {
+  using TA = typename dev::Acc<TV>::T;
+  int32_t c[U];
+  TV v[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    bool live = j + u < L && PJDS_IN(j + u, d.n_diag, dev::CHK_DIAG);
+    IDX o = 0;
+    if (live) {
+      o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
+      live = PJDS_IN(o, d.stored, dev::CHK_OFFSET);
+    }
+    if (live) {
+      c[u] = __ldcs(d.col + o);
+      if constexpr (!PAT) v[u] = dev::ld_stream1(val + o);
+    } else {
+      c[u] = -1;
+      v[u] = TV{};
+    }
+  }
+  TX xv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) xv[u] = gather_win(d, sx, x, c[u], a);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if constexpr (PAT)
+      acc = c[u] >= 0 ? acc + (TA)xv[u] : acc;
+    else
+      acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
+  }
+}
+
+// RT tiles per warp at a time (RT rows per thread, from different tiles), so
+// that each thread keeps RT independent chains of loads in flight.
+template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT>
 __global__ void __launch_bounds__(NT) pjds_window_kernel(const Desc d) {
   using TA = typename dev::Acc<TV>::T;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -80,54 +119,46 @@ __global__ void __launch_bounds__(NT) pjds_window_kernel(const Desc d) {
   for (int32_t e = threadIdx.x; e < (d.W + 31) / 32; e += NT) flag[e] = 0u;
   __syncthreads();
 
-  // 2. the window's tiles, one warp per tile
+  // 2. the window's tiles, RT per warp at a time
   const int32_t t0 = __ldg(d.win_ptr + blockIdx.x), t1 = __ldg(d.win_ptr + blockIdx.x + 1);
   const int32_t lane = threadIdx.x & 31;
-  for (int32_t t = t0 + (int32_t)(threadIdx.x >> 5); t < t1; t += NT / 32) {
-    const int32_t tile = __ldg(d.order + t);
-    if ((uint32_t)tile >= (uint32_t)(d.n_pad >> 5)) continue;
-    const int64_t i = (int64_t)tile * 32 + lane;
-    if (i >= d.n_rows || !PJDS_IN(i / d.b, d.n_blocks, dev::CHK_BLOCK)) continue;
-    const int32_t L = __ldg(d.block_len + (int32_t)(i / d.b));
-    TA acc = TA(0);
-    for (int32_t j = 0; j < L; j += U) {
-      int32_t c[U];
-      TV v[U];
+  for (int32_t t = t0 + RT * (int32_t)(threadIdx.x >> 5); t < t1; t += RT * (NT / 32)) {
+    int64_t i[RT];
+    int32_t L[RT];
+    int32_t Lmax = 0;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        bool live = j + u < L && PJDS_IN(j + u, d.n_diag, dev::CHK_DIAG);
-        IDX o = 0;
-        if (live) {
-          o = (IDX)__ldg(d.col_start + j + u) + (IDX)i;
-          live = PJDS_IN(o, d.stored, dev::CHK_OFFSET);
-        }
-        if (live) {
-          c[u] = __ldcs(d.col + o);
-          if constexpr (!PAT) v[u] = dev::ld_stream1(val + o);
-        } else {
-          c[u] = -1;
-          v[u] = TV{};
+    for (int r = 0; r < RT; ++r) {
+      L[r] = 0;
+      i[r] = -1;
+      if (t + r < t1) {
+        const int32_t tile = __ldg(d.order + t + r);
+        const int64_t ii = (int64_t)tile * 32 + lane;
+        if ((uint32_t)tile < (uint32_t)(d.n_pad >> 5) && ii < d.n_rows && PJDS_IN(ii / d.b, d.n_blocks, dev::CHK_BLOCK)) {
+          i[r] = ii;
+          L[r] = __ldg(d.block_len + (int32_t)(ii / d.b));
         }
       }
-      TX xv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) xv[u] = gather_win(d, sx, x, c[u], a);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if constexpr (PAT)
-          acc = c[u] >= 0 ? acc + (TA)xv[u] : acc;
-        else
-          acc = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u], acc) : acc;
-      }
+      Lmax = max(Lmax, L[r]);
     }
-    const int32_t p = __ldcs(d.perm + i);
-    if (!PJDS_IN(p, d.n_rows, dev::CHK_ROW)) continue;
-    const uint32_t r = (uint32_t)(p - a);
-    if (r < (uint32_t)d.W) {
-      sy[r] = (TX)acc;
-      atomicOr(flag + (r >> 5), 1u << (r & 31));
-    } else {
-      y[p] = (TX)acc;
+    TA acc[RT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) acc[r] = TA(0);
+    for (int32_t j = 0; j < Lmax; j += U) {
+#pragma unroll
+      for (int r = 0; r < RT; ++r) row_chunk<TV, TX, IDX, U, PAT>(d, val, sx, x, i[r], L[r], j, a, acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+      if (i[r] < 0) continue;
+      const int32_t p = __ldcs(d.perm + i[r]);
+      if (!PJDS_IN(p, d.n_rows, dev::CHK_ROW)) continue;
+      const uint32_t q = (uint32_t)(p - a);
+      if (q < (uint32_t)d.W) {
+        sy[q] = (TX)acc[r];
+        atomicOr(flag + (q >> 5), 1u << (q & 31));
+      } else {
+        y[p] = (TX)acc[r];
+      }
     }
   }
   __syncthreads();
