@@ -59,7 +59,7 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
       return set_error(PJDS_EINVAL, "window = 1 needs A's window plan, its tile_order and the original basis");
     if (c.unroll == 0) c.unroll = A->dtype == PJDS_F32 ? 8 : 4;
     if (c.unroll != 4 && c.unroll != 8) return set_error(PJDS_EINVAL, "unroll must be 4 or 8 with the window mapping");
-    c.block_threads = 512;
+    if (c.block_threads != 1024) c.block_threads = 512;
     c.tile_order = 1;
     return PJDS_OK;
   }
@@ -163,6 +163,9 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->rows_per_thread > 1 && !cfg->threads_per_row) c.threads_per_row = 1;
     if (cfg->threads_per_row > 1 && !cfg->rows_per_thread) c.rows_per_thread = 1;
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
+    // 1024 threads: the window mapping only (two window CTAs per SM)
+    if (cfg->block_threads == 1024 && cfg->window != 1)
+      return set_error(PJDS_EINVAL, "block_threads = 1024 needs window = 1");
     if (cfg->unroll) c.unroll = cfg->unroll;
     if (cfg->index64) c.index64 = 1;
     if (cfg->tile_order < -1 || cfg->tile_order > 1) return set_error(PJDS_EINVAL, "tile_order must be -1, 0 or 1");
@@ -194,7 +197,7 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
       c.rows_per_thread = cfg->rows_per_thread == 2 ? 2 : 1;
       c.threads_per_row = 1;
     } else if (cfg->window == -1 || cfg->plan || cfg->rows_per_thread || cfg->threads_per_row ||
-               cfg->block_threads || cfg->staged || cfg->tile_order) {
+               (cfg->block_threads && cfg->block_threads != 1024) || cfg->staged || cfg->tile_order) {
       if (c.window && !cfg->rows_per_thread && !cfg->threads_per_row) {
         // leaving the window mapping: back to the uniform default for this matrix
         const LaunchCfg u = [&] {

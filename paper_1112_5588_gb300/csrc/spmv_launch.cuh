@@ -114,9 +114,9 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
 }
 
 // Window mapping: one CTA per window of A->win_rows original rows (window.cuh).
-template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT>
-int launch_window_u(const win::Desc &d, size_t smem, int32_t n_win, cudaStream_t s) {
-  auto kern = win::pjds_window_kernel<TV, TX, IDX, U, RT, PAT>;
+template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT, int NT>
+int launch_window_nt(const win::Desc &d, size_t smem, int32_t n_win, cudaStream_t s) {
+  auto kern = win::pjds_window_kernel<TV, TX, IDX, U, RT, PAT, NT>;
   // the dynamic shared-memory limit is raised once per device (the kernel's
   // requirement is at most the plan's budget)
   static int raised[64] = {0};
@@ -127,8 +127,15 @@ int launch_window_u(const win::Desc &d, size_t smem, int32_t n_win, cudaStream_t
     if (e != cudaSuccess) return set_error(PJDS_ECUDA, "window kernel shared memory: %s", cudaGetErrorString(e));
     if (dev >= 0 && dev < 64) raised[dev] = 1;
   }
-  kern<<<(unsigned)n_win, win::NT, smem, s>>>(d);
+  kern<<<(unsigned)n_win, NT, smem, s>>>(d);
   return check_launch("pjds_spmv window launch");
+}
+
+// 512 or 1024 threads per window CTA
+template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT>
+int launch_window_u(const win::Desc &d, size_t smem, int32_t n_win, int nt, cudaStream_t s) {
+  if (nt == 1024) return launch_window_nt<TV, TX, IDX, U, RT, PAT, 1024>(d, smem, n_win, s);
+  return launch_window_nt<TV, TX, IDX, U, RT, PAT, 512>(d, smem, n_win, s);
 }
 
 template <typename TV, typename TX, typename IDX, bool SC>
@@ -169,16 +176,16 @@ int launch_window(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cud
   const bool two = c.rows_per_thread == 2;
   if (c.pattern) {
     if (two)
-      return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, true>(d, smem, A->n_win, s)
-                           : launch_window_u<TV, TX, IDX, 4, 2, true>(d, smem, A->n_win, s);
-    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, true>(d, smem, A->n_win, s)
-                         : launch_window_u<TV, TX, IDX, 4, 1, true>(d, smem, A->n_win, s);
+      return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, true>(d, smem, A->n_win, c.block_threads, s)
+                           : launch_window_u<TV, TX, IDX, 4, 2, true>(d, smem, A->n_win, c.block_threads, s);
+    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, true>(d, smem, A->n_win, c.block_threads, s)
+                         : launch_window_u<TV, TX, IDX, 4, 1, true>(d, smem, A->n_win, c.block_threads, s);
   }
   if (two)
-    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, false>(d, smem, A->n_win, s)
-                         : launch_window_u<TV, TX, IDX, 4, 2, false>(d, smem, A->n_win, s);
-  return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, false>(d, smem, A->n_win, s)
-                       : launch_window_u<TV, TX, IDX, 4, 1, false>(d, smem, A->n_win, s);
+    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, false>(d, smem, A->n_win, c.block_threads, s)
+                         : launch_window_u<TV, TX, IDX, 4, 2, false>(d, smem, A->n_win, c.block_threads, s);
+  return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, false>(d, smem, A->n_win, c.block_threads, s)
+                       : launch_window_u<TV, TX, IDX, 4, 1, false>(d, smem, A->n_win, c.block_threads, s);
 }
 
 // Per-tile mapping: one CTA per plan entry (tiles.cuh).

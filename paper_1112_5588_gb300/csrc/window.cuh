@@ -18,7 +18,6 @@
 namespace pjds {
 namespace win {
 
-constexpr int NT = 512;  // threads per window CTA
 constexpr int MAX_RANGES = 4;
 
 struct Desc {
@@ -94,8 +93,8 @@ __device__ __forceinline__ void row_chunk(const Desc &d, const TV *__restrict__ 
 
 // RT tiles per warp at a time (RT rows per thread, from different tiles), so
 // that each thread keeps RT independent chains of loads in flight.
-template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT>
-__global__ void __launch_bounds__(NT) pjds_window_kernel(const Desc d) {
+template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT, int NT>
+__global__ void __launch_bounds__(NT, 2048 / NT) pjds_window_kernel(const Desc d) {
   using TA = typename dev::Acc<TV>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   TX *sx = reinterpret_cast<TX *>(smem);
