@@ -531,9 +531,8 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
     out["pjds_f64_permuted_basis"] = {"gbs": round(b_pm / t_pm / 1e9, 1), "us": round(t_pm * 1e6, 2)}
     del Dp, xp, yp
 
-    for cfg in ({"window": -1}, {"rows_per_thread": 2}, {"rows_per_thread": 4}, {"threads_per_row": 2},
-                {"block_threads": 512}, {"block_threads": 128}, {"staged": 1}, {"tile_order": -1},
-                {"window": 1, "unroll": 8}):
+    for cfg in ({"rows_per_thread": 2}, {"rows_per_thread": 4}, {"threads_per_row": 2}, {"block_threads": 512},
+                {"block_threads": 128}, {"staged": 1}, {"tile_order": -1}):
         tc = med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xt, y, **cfg), K, W, flush))
         key = "cfg_" + "_".join(f"{k}{v}" for k, v in cfg.items())
         out[key] = {"gbs": round(nbytes / tc / 1e9, 1), "us": round(tc * 1e6, 2)}
@@ -927,7 +926,6 @@ def run_case(argv) -> int:
     ap.add_argument("--staged", action="store_true")
     ap.add_argument("--threads-per-row", type=int, default=0)
     ap.add_argument("--rows-per-thread", type=int, default=0)
-    ap.add_argument("--window", type=int, default=0, help="0 automatic, 1 the window mapping, -1 not")
     ap.add_argument("--tile-order", type=int, default=0)
     ap.add_argument("--plan", type=int, default=0)
     ap.add_argument("--unroll", type=int, default=0)
@@ -973,7 +971,7 @@ def run_case(argv) -> int:
             run = lambda: pjds.ellr_spmv(D, x, y)  # noqa: E731
         else:
             kw = dict(staged=1 if a.staged else 0, threads_per_row=a.threads_per_row,
-                      rows_per_thread=a.rows_per_thread, window=a.window, tile_order=a.tile_order, plan=a.plan,
+                      rows_per_thread=a.rows_per_thread, tile_order=a.tile_order, plan=a.plan,
                       unroll=a.unroll, block_threads=a.block_threads)
             run = (lambda: pjds.pjds_spmv_pattern(D, x, y, **kw)) if a.kind == "pattern" else (  # noqa: E731
                 lambda: pjds.pjds_spmv_cfg(D, x, y, **kw))

@@ -89,13 +89,6 @@ void pjds_abi_sizes(int32_t out[5]);
  * per-tile mapping, the sorted rows cut into one-CTA tiles each mapped by its
  * block's length (see pjds_dev). It assumes 16-byte aligned device arrays;
  * the launcher checks.
- * win_ptr, n_win, win_rows, win_lo, win_len and n_win_ranges are the window
- * mapping (see pjds_dev), not part of the format either. pjds_create builds
- * it in the original basis for a matrix of at least 2^16 rows whose entries
- * sit mostly on a few offsets col - row (a band structure): the offsets that
- * occur in at least 1/8 of the rows (searched within +-2^16) must hold a
- * quarter of the entries or more. Otherwise win_ptr is NULL and the other
- * fields are 0.
  */
 typedef struct pjds_host {
   int32_t n_rows, n_cols, n_pad, b, n_blocks, n_max;
@@ -111,10 +104,6 @@ typedef struct pjds_host {
   int32_t *tile_order; /* [n_pad / 32] */
   int32_t *plan;       /* [4 * n_plan] per-tile mapping, see pjds_dev */
   int32_t n_plan, plan_reserved;
-  int32_t *win_ptr;    /* [n_win + 1] window mapping, see pjds_dev; NULL when none */
-  int32_t n_win, win_rows;
-  int32_t win_lo[4], win_len[4];
-  int32_t n_win_ranges, win_reserved;
 } pjds_host;
 
 /*
@@ -138,16 +127,6 @@ typedef struct pjds_host {
  * the uniform mappings (one thread per row for kinds 0 and 3). The plan
  * kernel runs one CTA per entry; it needs plan, val and col 16-byte aligned
  * and skips an entry that does not describe a tile of the matrix.
- * win_ptr (n_win + 1 int32, with the window fields copied from the host
- * struct) is the window mapping pjds_create wrote, or NULL. Window w holds
- * the tiles tile_order[win_ptr[w] .. win_ptr[w+1]), the tiles whose first
- * row lies in the original rows [w win_rows, (w+1) win_rows); one CTA runs
- * a window. It copies the intervals x[a + win_lo[k], a + win_lo[k] +
- * win_len[k]) (a = w win_rows, k < n_win_ranges <= 4: the band offsets of
- * its rows) into shared memory and takes x[c] from there when c lies in one,
- * and it writes the sums of the rows inside its window as whole lines at the
- * end. Each thread runs one row as the one-thread-per-row mapping does (same
- * bits). The window mapping needs tile_order and the original basis.
  * val must be 16-byte aligned; all other pointers 4-byte aligned.
  */
 typedef struct pjds_dev {
@@ -163,10 +142,6 @@ typedef struct pjds_dev {
   const int32_t *tile_order; /* NULL: tiles in sorted order */
   const int32_t *plan;       /* NULL: no per-tile mapping */
   int32_t n_plan, plan_reserved;
-  const int32_t *win_ptr;    /* NULL: no window mapping */
-  int32_t n_win, win_rows;
-  int32_t win_lo[4], win_len[4];
-  int32_t n_win_ranges, win_reserved;
 } pjds_dev;
 
 /*
@@ -259,17 +234,8 @@ int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
  *                    default takes 0.870 / 0.941 / 0.980 of the best uniform
  *                    mapping's time (fp64 / fp32 / bf16, geometric mean).
  *                    With the plan the other fields do not apply.
- *   window           0: automatic, 1: the window mapping of A->win_ptr
- *                    (PJDS_EINVAL if A has none, or no tile_order, or is in
- *                    the permuted basis), -1: not. One thread per row; unroll
- *                    4 or 8 (0 = default); block_threads does not apply (512).
- *                    Automatic uses it when A has one, unless the caller asks
- *                    for another mapping (plan = 1, staged, or any of
- *                    rows_per_thread, threads_per_row, block_threads,
- *                    tile_order set).
  * rows_per_thread > 1 and threads_per_row > 1 are exclusive, and staged
- * excludes plan = 1 and window = 1; plan = 1 excludes window = 1. Invalid
- * values return PJDS_EINVAL.
+ * excludes plan = 1. Invalid values return PJDS_EINVAL.
  */
 typedef struct pjds_launch {
   int32_t rows_per_thread;
@@ -281,8 +247,6 @@ typedef struct pjds_launch {
                        used automatically from 2^31 stored entries on) */
   int32_t tile_order; /* 0 automatic, 1 the traversal table, -1 sorted order */
   int32_t plan;       /* 0 automatic, 1 the per-tile mapping of A->plan, -1 a uniform mapping */
-  int32_t window;     /* 0 automatic, 1 the window mapping of A->win_ptr, -1 not */
-  int32_t reserved;   /* 0 */
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);

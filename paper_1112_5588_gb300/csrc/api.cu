@@ -2,8 +2,6 @@
 // changes): argument checks, the default kernel configuration, dtype dispatch.
 #include <stdint.h>
 
-#include <algorithm>
-
 #include "common.h"
 #include "spmv_launch.cuh"
 
@@ -24,15 +22,6 @@ static int check_pjds_dev(const pjds_dev *A, const void *x, const void *y, bool 
   // a plan holds at most one tile per 32 rows
   if (A->plan && (A->n_plan < 0 || A->n_plan > A->n_pad / 32))
     return set_error(PJDS_EINVAL, "n_plan %d outside [0, %d]", A->n_plan, A->n_pad / 32);
-  // a window plan: one window per win_rows rows, at most four intervals
-  if (A->win_ptr) {
-    if (A->win_rows <= 0 || A->n_win != (int32_t)(((int64_t)A->n_rows + A->win_rows - 1) / std::max(A->win_rows, 1)) ||
-        A->n_win_ranges < 0 || A->n_win_ranges > 4)
-      return set_error(PJDS_EINVAL, "window fields inconsistent (n_win %d, win_rows %d, ranges %d)", A->n_win,
-                       A->win_rows, A->n_win_ranges);
-    for (int k = 0; k < A->n_win_ranges; ++k)
-      if (A->win_len[k] <= 0) return set_error(PJDS_EINVAL, "window interval %d is empty", k);
-  }
   return PJDS_OK;
 }
 
@@ -51,18 +40,6 @@ static int dispatch_pjds(const pjds_dev *A, const void *x, void *y, const Launch
 }
 
 static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
-  if (c.window) {
-    if (c.staged || c.plan) return set_error(PJDS_EINVAL, "the window mapping excludes staged and plan = 1");
-    if ((c.rows_per_thread != 1 && c.rows_per_thread != 2) || c.threads_per_row != 1)
-      return set_error(PJDS_EINVAL, "the window mapping runs one thread per row, one or two rows per thread");
-    if (!window_usable(A))
-      return set_error(PJDS_EINVAL, "window = 1 needs A's window plan, its tile_order and the original basis");
-    if (c.unroll == 0) c.unroll = A->dtype == PJDS_F32 ? 8 : 4;
-    if (c.unroll != 4 && c.unroll != 8) return set_error(PJDS_EINVAL, "unroll must be 4 or 8 with the window mapping");
-    if (c.block_threads != 1024) c.block_threads = 512;
-    c.tile_order = 1;
-    return PJDS_OK;
-  }
   const int R = c.rows_per_thread, T = c.threads_per_row;
   if (R != 1 && R != 2 && R != 4) return set_error(PJDS_EINVAL, "rows_per_thread must be 1, 2 or 4");
   if (T != 1 && T != 2 && T != 4 && T != 8) return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
@@ -131,11 +108,6 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   c.index64 = 0;
   c.tile_order = auto_tile_order(A) ? 1 : 0;
   c.plan = auto_plan(A) ? 1 : 0;
-  c.window = !c.plan && auto_window(A) ? 1 : 0;
-  if (c.window) {
-    c.rows_per_thread = 1;
-    c.threads_per_row = 1;
-  }
   return c;
 }
 
@@ -163,9 +135,6 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->rows_per_thread > 1 && !cfg->threads_per_row) c.threads_per_row = 1;
     if (cfg->threads_per_row > 1 && !cfg->rows_per_thread) c.rows_per_thread = 1;
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
-    // 1024 threads: the window mapping only (two window CTAs per SM)
-    if (cfg->block_threads == 1024 && cfg->window != 1)
-      return set_error(PJDS_EINVAL, "block_threads = 1024 needs window = 1");
     if (cfg->unroll) c.unroll = cfg->unroll;
     if (cfg->index64) c.index64 = 1;
     if (cfg->tile_order < -1 || cfg->tile_order > 1) return set_error(PJDS_EINVAL, "tile_order must be -1, 0 or 1");
@@ -180,36 +149,8 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
       if (cfg->staged) return set_error(PJDS_EINVAL, "staged and plan = 1 are exclusive");
       c.plan = 1;
     } else if (cfg->plan == -1 || cfg->rows_per_thread || cfg->threads_per_row || cfg->block_threads ||
-               cfg->unroll || cfg->staged || cfg->tile_order || cfg->window == 1) {
+               cfg->unroll || cfg->staged || cfg->tile_order) {
       c.plan = 0;
-    }
-    // the window mapping: forced, switched off, or automatic unless the caller
-    // asked for another mapping
-    if (cfg->window < -1 || cfg->window > 1) return set_error(PJDS_EINVAL, "window must be -1, 0 or 1");
-    if (cfg->reserved != 0) return set_error(PJDS_EINVAL, "pjds_launch.reserved must be 0");
-    if (cfg->window == 1) {
-      if (cfg->plan == 1) return set_error(PJDS_EINVAL, "plan = 1 and window = 1 are exclusive");
-      if (cfg->staged) return set_error(PJDS_EINVAL, "staged and window = 1 are exclusive");
-      if (cfg->rows_per_thread > 2 || cfg->threads_per_row > 1)
-        return set_error(PJDS_EINVAL, "the window mapping runs one thread per row, one or two rows per thread");
-      c.window = 1;
-      c.plan = 0;
-      c.rows_per_thread = cfg->rows_per_thread == 2 ? 2 : 1;
-      c.threads_per_row = 1;
-    } else if (cfg->window == -1 || cfg->plan || cfg->rows_per_thread || cfg->threads_per_row ||
-               (cfg->block_threads && cfg->block_threads != 1024) || cfg->staged || cfg->tile_order) {
-      if (c.window && !cfg->rows_per_thread && !cfg->threads_per_row) {
-        // leaving the window mapping: back to the uniform default for this matrix
-        const LaunchCfg u = [&] {
-          pjds_dev B = *A;
-          B.win_ptr = nullptr;
-          return default_cfg(&B);
-        }();
-        if (!cfg->rows_per_thread) c.rows_per_thread = u.rows_per_thread;
-        if (!cfg->threads_per_row) c.threads_per_row = u.threads_per_row;
-        if (!cfg->block_threads) c.block_threads = u.block_threads;
-      }
-      c.window = 0;
     }
     if (cfg->staged) {
       c.staged = 1;
@@ -236,8 +177,6 @@ extern "C" int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds
   out->index64 = c.index64;
   out->tile_order = c.tile_order ? 1 : -1;
   out->plan = c.plan ? 1 : -1;
-  out->window = c.window ? 1 : -1;
-  out->reserved = 0;
   return PJDS_OK;
 }
 
@@ -258,8 +197,8 @@ extern "C" int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, cons
   LaunchCfg c;
   rc = resolve_cfg(A, cfg, c);
   if (rc) return rc;
-  if (c.plan || c.staged || c.threads_per_row != 1 || (c.rows_per_thread != 1 && !c.window))
-    return set_error(PJDS_EINVAL, "the pattern product runs the one-thread-per-row mappings only (uniform or window)");
+  if (c.plan || c.staged || c.rows_per_thread != 1 || c.threads_per_row != 1)
+    return set_error(PJDS_EINVAL, "the pattern product runs the one-thread-per-row mappings only");
   c.pattern = 1;
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
 }

@@ -55,18 +55,4 @@ inline bool auto_plan(const pjds_dev *A) {
   return plan_usable(A) && A->n_rows >= min_rows && (int64_t)A->n_max * A->n_rows > 4 * A->nnz;
 }
 
-// Whether the window mapping can run: a window plan, the traversal table it
-// is built on, the original basis.
-inline bool window_usable(const pjds_dev *A) {
-  return A->win_ptr && A->n_win > 0 && A->win_rows > 0 && A->n_win_ranges > 0 && A->n_win_ranges <= 4 &&
-         A->tile_order && !A->permute_cols;
-}
-
-// Default use of the window mapping: a matrix that has one (pjds_create builds
-// it for band-structured matrices of at least 2^16 rows) and whose longest
-// row is at most 4 times the mean (wider spreads take the per-tile mapping).
-inline bool auto_window(const pjds_dev *A) {
-  return window_usable(A) && (int64_t)A->n_max * A->n_rows <= 4 * A->nnz;
-}
-
 }  // namespace pjds

@@ -19,7 +19,6 @@
 
 #include "common.h"
 #include "plan.h"
-#include "window.h"
 
 namespace pjds {
 
@@ -112,7 +111,6 @@ static void free_pjds(pjds_host *h) {
   free(h->val);
   free(h->tile_order);
   free(h->plan);
-  free(h->win_ptr);
   free(h);
 }
 
@@ -135,7 +133,7 @@ using namespace pjds;
 
 extern "C" const char *pjds_last_error(void) { return g_msg; }
 
-extern "C" int32_t pjds_version(void) { return 5; }
+extern "C" int32_t pjds_version(void) { return 4; }
 
 extern "C" void pjds_abi_sizes(int32_t out[5]) {
   out[0] = (int32_t)sizeof(pjds_host);
@@ -279,26 +277,6 @@ extern "C" int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_pt
       h->plan[4 * t + 1] = cut[t].row0;
       h->plan[4 * t + 2] = cut[t].rows;
       h->plan[4 * t + 3] = cut[t].kind;
-    }
-  }
-
-  // window mapping, for band-structured matrices in the original basis
-  if (!permute_cols) {
-    WindowPlan wp;
-    if (window_plan_build(n_rows, row_ptr, col_idx, perm, h->tile_order, n_tiles, vector_bytes(dtype), wp)) {
-      h->win_ptr = alloc_n<int32_t>((int64_t)wp.win_ptr.size());
-      if (!h->win_ptr) {
-        free_pjds(h);
-        return set_error(PJDS_ENOMEM, "out of host memory");
-      }
-      std::copy(wp.win_ptr.begin(), wp.win_ptr.end(), h->win_ptr);
-      h->n_win = (int32_t)wp.win_ptr.size() - 1;
-      h->win_rows = wp.W;
-      h->n_win_ranges = wp.n_ranges;
-      for (int k = 0; k < WIN_MAX_RANGES; ++k) {
-        h->win_lo[k] = wp.lo[k];
-        h->win_len[k] = wp.len[k];
-      }
     }
   }
   *out = h;

@@ -10,7 +10,6 @@
 #include "spmv_kernels.cuh"
 #include "spmv_staged.cuh"
 #include "tiles.cuh"
-#include "window.cuh"
 
 namespace pjds {
 
@@ -24,7 +23,6 @@ struct LaunchCfg {
   int tile_order;       // 1: tiles taken in A->tile_order
   int plan;             // 1: per-tile mapping of A->plan (the fields above do not apply)
   int pattern = 0;      // 1: the pattern product (values taken as 1, val not read)
-  int window = 0;       // 1: the window mapping of A->win_ptr (R = T = 1)
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -53,12 +51,8 @@ int launch_staged(const pjds_dev *A, const TX *x, TX *y, cudaStream_t s) {
 }
 
 template <typename TV, typename TX, typename IDX, bool SC>
-int launch_window(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaStream_t s);
-
-template <typename TV, typename TX, typename IDX, bool SC>
 int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaStream_t s) {
   if (c.staged) return launch_staged<TV, TX, IDX, SC>(A, x, y, s);
-  if (c.window) return launch_window<TV, TX, IDX, SC>(A, x, y, c, s);
   const TV *val = static_cast<const TV *>(A->val);
   const int R = c.rows_per_thread, T = c.threads_per_row, nt = c.block_threads;
   const int64_t work = T > 1 ? (int64_t)A->n_pad * T : ((int64_t)A->n_pad + R - 1) / R;
@@ -111,81 +105,6 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
 #undef PJDS_TPR
 #undef PJDS_ARGS
   return check_launch("pjds_spmv launch");
-}
-
-// Window mapping: one CTA per window of A->win_rows original rows (window.cuh).
-template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT, int NT>
-int launch_window_nt(const win::Desc &d, size_t smem, int32_t n_win, cudaStream_t s) {
-  auto kern = win::pjds_window_kernel<TV, TX, IDX, U, RT, PAT, NT>;
-  // the dynamic shared-memory limit is raised once per device (the kernel's
-  // requirement is at most the plan's budget)
-  static int raised[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !raised[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "window kernel shared memory: %s", cudaGetErrorString(e));
-    if (dev >= 0 && dev < 64) raised[dev] = 1;
-  }
-  kern<<<(unsigned)n_win, NT, smem, s>>>(d);
-  return check_launch("pjds_spmv window launch");
-}
-
-// 512 or 1024 threads per window CTA
-template <typename TV, typename TX, typename IDX, int U, int RT, bool PAT>
-int launch_window_u(const win::Desc &d, size_t smem, int32_t n_win, int nt, cudaStream_t s) {
-  if (nt == 1024) return launch_window_nt<TV, TX, IDX, U, RT, PAT, 1024>(d, smem, n_win, s);
-  return launch_window_nt<TV, TX, IDX, U, RT, PAT, 512>(d, smem, n_win, s);
-}
-
-template <typename TV, typename TX, typename IDX, bool SC>
-int launch_window(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaStream_t s) {
-  if (!SC) return set_error(PJDS_EINVAL, "the window mapping runs in the original basis only");
-  if (A->n_win <= 0 || A->n_rows == 0) return PJDS_OK;
-  win::Desc d;
-  d.val = A->val;
-  d.col = A->col;
-  d.col_start = A->col_start;
-  d.block_len = A->block_len;
-  d.perm = A->perm;
-  d.order = A->tile_order;
-  d.win_ptr = A->win_ptr;
-  d.x = x;
-  d.y = y;
-  d.stored = A->n_stored;
-  d.n_rows = A->n_rows;
-  d.n_cols = A->n_cols;
-  d.n_pad = A->n_pad;
-  d.b = A->b;
-  d.W = A->win_rows;
-  d.n_ranges = A->n_win_ranges;
-  d.n_blocks = A->n_blocks;
-  d.n_diag = A->n_max + 1;
-  int32_t off = 0;
-  for (int k = 0; k < win::MAX_RANGES; ++k) {
-    const bool on = k < d.n_ranges;
-    d.lo[k] = on ? A->win_lo[k] : 0;
-    d.len[k] = on ? A->win_len[k] : 0;
-    d.soff[k] = off;
-    off += on ? (d.len[k] + 1) / 2 * 2 : 0;
-  }
-  d.staged = off;
-  d.reserved = 0;
-  const size_t smem = ((size_t)off + (size_t)d.W) * sizeof(TX) + ((size_t)d.W + 31) / 32 * 4;
-  if (smem > 160 * 1024) return set_error(PJDS_EINVAL, "window plan needs %zu bytes of shared memory", smem);
-  const bool two = c.rows_per_thread == 2;
-  if (c.pattern) {
-    if (two)
-      return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, true>(d, smem, A->n_win, c.block_threads, s)
-                           : launch_window_u<TV, TX, IDX, 4, 2, true>(d, smem, A->n_win, c.block_threads, s);
-    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, true>(d, smem, A->n_win, c.block_threads, s)
-                         : launch_window_u<TV, TX, IDX, 4, 1, true>(d, smem, A->n_win, c.block_threads, s);
-  }
-  if (two)
-    return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 2, false>(d, smem, A->n_win, c.block_threads, s)
-                         : launch_window_u<TV, TX, IDX, 4, 2, false>(d, smem, A->n_win, c.block_threads, s);
-  return c.unroll == 8 ? launch_window_u<TV, TX, IDX, 8, 1, false>(d, smem, A->n_win, c.block_threads, s)
-                       : launch_window_u<TV, TX, IDX, 4, 1, false>(d, smem, A->n_win, c.block_threads, s);
 }
 
 // Per-tile mapping: one CTA per plan entry (tiles.cuh).

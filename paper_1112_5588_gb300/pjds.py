@@ -44,23 +44,19 @@ class _PjdsHostS(ctypes.Structure):
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("inv_perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp),
                 ("col", _vp), ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32),
-                ("plan_reserved", _i32), ("win_ptr", _vp), ("n_win", _i32), ("win_rows", _i32),
-                ("win_lo", _i32 * 4), ("win_len", _i32 * 4), ("n_win_ranges", _i32), ("win_reserved", _i32)]
+                ("plan_reserved", _i32)]
 
 
 class _PjdsDevS(ctypes.Structure):
     _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp), ("col", _vp),
-                ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32), ("plan_reserved", _i32),
-                ("win_ptr", _vp), ("n_win", _i32), ("win_rows", _i32), ("win_lo", _i32 * 4), ("win_len", _i32 * 4),
-                ("n_win_ranges", _i32), ("win_reserved", _i32)]
+                ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32), ("plan_reserved", _i32)]
 
 
 class _LaunchS(ctypes.Structure):
     _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32),
-                ("staged", _i32), ("index64", _i32), ("tile_order", _i32), ("plan", _i32), ("window", _i32),
-                ("reserved", _i32)]
+                ("staged", _i32), ("index64", _i32), ("tile_order", _i32), ("plan", _i32)]
 
 
 class _EllrHostS(ctypes.Structure):
@@ -179,30 +175,20 @@ class PjdsHost:
         self.n_plan = int(s.n_plan)
         # per-tile mapping: n_plan rows of (0, first sorted row, rows, kind)
         self.plan = _np_view(s.plan, 4 * s.n_plan, np.int32).reshape(-1, 4)
-        # window mapping: n_win + 1 positions in tile_order, the window size
-        # and the staged x intervals (empty when the matrix has none)
-        self.n_win, self.win_rows, self.n_win_ranges = int(s.n_win), int(s.win_rows), int(s.n_win_ranges)
-        self.win_ptr = _np_view(s.win_ptr, s.n_win + 1 if s.win_ptr else 0, np.int32)
-        self.win_lo = [int(v) for v in s.win_lo]
-        self.win_len = [int(v) for v in s.win_len]
 
     def arrays(self) -> dict:
         """Copies of every array plus the sizes (survive destroy())."""
         out = {k: getattr(self, k) for k, _ in _PjdsHostS._fields_[:10]}
-        for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val", "tile_order", "plan",
-                  "win_ptr"):
+        for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val", "tile_order", "plan"):
             out[k] = getattr(self, k).copy()
-        for k in ("n_plan", "n_win", "win_rows", "n_win_ranges", "win_lo", "win_len"):
-            out[k] = getattr(self, k)
+        out["n_plan"] = self.n_plan
         return out
 
-    def to_device(self, device="cuda", tile_order: bool = True, plan: bool = True,
-                  window: bool = True) -> "PjdsDevice":
+    def to_device(self, device="cuda", tile_order: bool = True, plan: bool = True) -> "PjdsDevice":
         """Upload; tile_order=False leaves the traversal table out (tiles in
-        sorted order; no window mapping either), plan=False the per-tile
-        mapping, window=False the window mapping (uniform mappings only):
+        sorted order), plan=False the per-tile mapping (uniform mappings only):
         same results, for comparisons."""
-        return PjdsDevice(self, device, tile_order, plan, window)
+        return PjdsDevice(self, device, tile_order, plan)
 
     def destroy(self):
         if self._ptr is not None:
@@ -231,8 +217,7 @@ def pjds_create(n_rows: int, n_cols: int, row_ptr, col, val, b: int = 32, dtype=
 class PjdsDevice:
     """Device copy of a pJDS matrix in torch-owned buffers plus its pjds_dev struct."""
 
-    def __init__(self, host: PjdsHost, device="cuda", tile_order: bool = True, plan: bool = True,
-                 window: bool = True):
+    def __init__(self, host: PjdsHost, device="cuda", tile_order: bool = True, plan: bool = True):
         dev = torch.device(device)
         self.device = dev
         self.dtype = host.dtype
@@ -253,9 +238,6 @@ class PjdsDevice:
         self.tile_order = up(host.tile_order, np.int32) if tile_order else None
         self.n_plan = host.n_plan if plan else 0
         self.plan = up(host.plan, np.int32) if plan and host.n_plan > 0 else None
-        use_win = window and tile_order and host.n_win > 0
-        self.win_ptr = up(host.win_ptr, np.int32) if use_win else None
-        self.n_win = host.n_win if use_win else 0
         s = _PjdsDevS()
         for f, _ in _PjdsDevS._fields_[:10]:
             setattr(s, f, getattr(host, f))
@@ -268,11 +250,6 @@ class PjdsDevice:
         s.tile_order = (self.tile_order.data_ptr() or None) if tile_order else None
         s.plan = self.plan.data_ptr() if self.plan is not None else None
         s.n_plan = self.n_plan if self.plan is not None else 0
-        if use_win:
-            s.win_ptr = self.win_ptr.data_ptr()
-            s.n_win, s.win_rows, s.n_win_ranges = host.n_win, host.win_rows, host.n_win_ranges
-            s.win_lo[:] = host.win_lo
-            s.win_len[:] = host.win_len
         self._s = s
 
     @property
@@ -281,8 +258,7 @@ class PjdsDevice:
 
     def device_bytes(self) -> int:
         return sum(t.numel() * t.element_size() for t in (self.perm, self.block_len, self.row_len, self.col_start,
-                                                           self.col, self.val, self.tile_order, self.plan,
-                                                           self.win_ptr)
+                                                           self.col, self.val, self.tile_order, self.plan)
                    if t is not None)
 
 
@@ -303,16 +279,13 @@ def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> t
 
 def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
                   threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, staged: int = 0,
-                  index64: int = 0, tile_order: int = 0, plan: int = 0, window: int = 0,
-                  stream=None) -> torch.Tensor:
+                  index64: int = 0, tile_order: int = 0, plan: int = 0, stream=None) -> torch.Tensor:
     """y = A x with an explicit kernel configuration (pjds_spmv_cfg).
     tile_order: 0 automatic, 1 traversal table, -1 sorted order; plan: 0
-    automatic, 1 the per-tile mapping, -1 a uniform mapping; window: 0
-    automatic, 1 the window mapping, -1 not."""
+    automatic, 1 the per-tile mapping, -1 a uniform mapping."""
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan,
-                   window, 0)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y
@@ -324,7 +297,7 @@ def pjds_spmv_pattern(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=No
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
     keys = ("rows_per_thread", "threads_per_row", "block_threads", "unroll", "staged", "index64", "tile_order",
-            "plan", "window")
+            "plan")
     c = _LaunchS(*[int(cfg.pop(k, 0)) for k in keys])
     if cfg:
         raise TypeError(f"unknown launch fields {sorted(cfg)}")
@@ -334,18 +307,16 @@ def pjds_spmv_pattern(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=No
 
 
 def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, block_threads: int = 0,
-                      unroll: int = 0, staged: int = 0, index64: int = 0, tile_order: int = 0, plan: int = 0,
-                      window: int = 0) -> dict:
+                      unroll: int = 0, staged: int = 0, index64: int = 0, tile_order: int = 0, plan: int = 0) -> dict:
     """The launch configuration pjds_spmv_cfg would use (no launch). `A` is a
     PjdsDevice or a PjdsHost (only sizes and alignment are read)."""
     s = A.struct if isinstance(A, PjdsDevice) else _dev_struct_from_host(A)
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan,
-                   window, 0)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan)
     out = _LaunchS()
     _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
             "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged,
-            "index64": out.index64, "tile_order": out.tile_order, "plan": out.plan, "window": out.window}
+            "index64": out.index64, "tile_order": out.tile_order, "plan": out.plan}
 
 
 def pjds_check_word(clear: bool = True, stream=None) -> int:
@@ -377,11 +348,6 @@ def _dev_struct_from_host(H: "PjdsHost"):
     s.tile_order = 512 if len(H.tile_order) else None
     s.plan = 512 if H.n_plan else None
     s.n_plan = H.n_plan
-    if H.n_win > 0:
-        s.win_ptr = 512
-        s.n_win, s.win_rows, s.n_win_ranges = H.n_win, H.win_rows, H.n_win_ranges
-        s.win_lo[:] = H.win_lo
-        s.win_len[:] = H.win_len
     return s
 
 

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(P):
 
 
 def test_abi_version_and_struct_sizes(P):
-    assert P.lib().pjds_version() == 5  # the binding itself checked the struct sizes on load
+    assert P.lib().pjds_version() == 4  # the binding itself checked the struct sizes on load
 
 
 CASES = [
@@ -219,7 +219,7 @@ def test_resolve_defaults(P):
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32)
     # 10k rows: one thread per row would leave the GPU short of threads
     assert P.pjds_spmv_resolve(H) == {"rows_per_thread": 1, "threads_per_row": 8, "block_threads": 128, "unroll": 4,
-                                      "staged": 0, "index64": 0, "tile_order": -1, "plan": -1, "window": -1}
+                                      "staged": 0, "index64": 0, "tile_order": -1, "plan": -1}
     # both sides of every threshold: the thread floor (2^17 rows at T = 1,
     # 2^16 at T = 2, ...) and the chain ratio (a long row of growing length)
     seen = set()
@@ -231,7 +231,7 @@ def test_resolve_defaults(P):
         n_max = int(np.diff(C.row_ptr).max())
         for dt in ("f64", "f32", "bf16"):
             HC = P.pjds_create(C.n_rows, C.n_cols, C.row_ptr, C.col, C.val, b=32, dtype=dt)
-            r = P.pjds_spmv_resolve(HC, window=-1)  # the uniform rule (band matrices have a window plan)
+            r = P.pjds_spmv_resolve(HC)
             t = _expected_threads_per_row(n, n_max, C.nnz, dt)
             assert r["threads_per_row"] == t and r["rows_per_thread"] == 1, (n, long_len, dt, r, t)
             assert r["block_threads"] == (256 if t == 1 or dt == "f32" else 128), (n, dt, r)
@@ -259,20 +259,19 @@ def test_resolve_large_matrix_defaults(P):
     C = _band(1 << 21, 3)
     for dt, R in (("f64", 1), ("f32", 2), ("bf16", 2)):
         H = P.pjds_create(C.n_rows, C.n_cols, C.row_ptr, C.col, C.val, b=32, dtype=dt)
-        r = P.pjds_spmv_resolve(H, window=-1)
+        r = P.pjds_spmv_resolve(H)
         assert (r["threads_per_row"], r["rows_per_thread"], r["block_threads"], r["unroll"]) == (1, R, 256, 4), (dt, r)
         # asking for several threads per row implies one row per thread
         assert P.pjds_spmv_resolve(H, threads_per_row=2)["rows_per_thread"] == 1
         s = P._dev_struct_from_host(H)
         s.val = 514  # not aligned for paired loads: one row per thread
-        s.win_ptr = None
         out = P._LaunchS()
         assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(out)) == 0
         assert out.rows_per_thread == 1
         H.destroy()
     C = _band((1 << 21) - 1, 3)
     H = P.pjds_create(C.n_rows, C.n_cols, C.row_ptr, C.col, C.val, b=32, dtype="f32")
-    assert P.pjds_spmv_resolve(H, window=-1)["rows_per_thread"] == 1
+    assert P.pjds_spmv_resolve(H)["rows_per_thread"] == 1
 
 
 def test_resolve_tile_order_rule(P):
@@ -284,7 +283,7 @@ def test_resolve_tile_order_rule(P):
     assert P.pjds_spmv_resolve(big, tile_order=-1)["tile_order"] == -1
     assert P.pjds_spmv_resolve(big, staged=1)["tile_order"] == -1
     small = P.pjds_create(*(lambda C: (C.n_rows, C.n_cols, C.row_ptr, C.col, C.val))(_band((1 << 20) - 1, 3)), b=32)
-    assert P.pjds_spmv_resolve(small, window=-1)["tile_order"] == -1
+    assert P.pjds_spmv_resolve(small)["tile_order"] == -1
     assert P.pjds_spmv_resolve(small, tile_order=1)["tile_order"] == 1
     spread = P.pjds_create(*(lambda C: (C.n_rows, C.n_cols, C.row_ptr, C.col, C.val))(
         _band(1 << 20, 3, long_row=5)), b=32)  # longest 64 > 4 x mean (~3)
