@@ -10,7 +10,7 @@
  * speed of pJDS vs ELLPACK-R follow the histogram's width) and on RHS reuse
  * (Eq. 1, alpha); the features below summarise both.
  *
- * Model: 13 inputs -> 64 ReLU -> 64 ReLU -> 1, fp32, inputs and target
+ * Model: 15 inputs -> 64 ReLU -> 64 ReLU -> 1, fp32, inputs and target
  * standardised with the statistics stored in the model. Training (full or
  * mini-batch Adam on the mean squared error of the standardised log time) and
  * inference run in hand-written CUDA kernels; gradients are summed per CTA
@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define PJDS_MLP_IN 13
+#define PJDS_MLP_IN 15
 #define PJDS_MLP_HID 64
 #define PJDS_MLP_FEATURES 8
 
@@ -41,11 +41,18 @@ typedef struct pjds_mlp {
   float w3[PJDS_MLP_HID], b3;
   float in_mean[PJDS_MLP_IN], in_std[PJDS_MLP_IN];
   float out_mean, out_std;
+  /* the matrix features the model was trained on span [feat_lo, feat_hi]
+   * (pjds_mlp_fit_range); feat_lo > feat_hi means no range is set */
+  float feat_lo[PJDS_MLP_FEATURES], feat_hi[PJDS_MLP_FEATURES];
 } pjds_mlp;
 
 /* He-uniform weights from a counter-based generator, zero biases, identity
- * standardisation (mean 0, std 1). */
+ * standardisation (mean 0, std 1), no feature range. */
 int pjds_mlp_init(pjds_mlp *m, uint64_t seed);
+
+/* Set the model's feature range from the features of its n training
+ * matrices, feat[n][8] (host): per feature the smallest and largest value. */
+int pjds_mlp_fit_range(pjds_mlp *m, const float *feat, int32_t n);
 
 /* Set the model's standardisation from n samples X[n][13], y[n] (host):
  * population mean and standard deviation per column (1 where it is 0). */
@@ -81,8 +88,45 @@ int pjds_features(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const 
                   float out[PJDS_MLP_FEATURES]);
 
 /* Model inputs for n candidates: the 8 features, then log2(b / 32),
- * log2(threads per row), and a one-hot dtype (f64, f32, bf16). */
+ * log2(threads per row) (0 for the per-tile mapping), a one-hot dtype (f64,
+ * f32, bf16), 1 for the per-tile mapping (plan = 1) else 0, and 1 when the
+ * tiles are taken in the traversal table (tile_order = 1) else 0. */
 int pjds_tune_encode(const float feat[PJDS_MLP_FEATURES], const pjds_candidate *cands, int32_t n, float *out);
+
+#define PJDS_PICK_MODEL 0 /* the model's smallest predicted time */
+#define PJDS_PICK_SWEEP 1 /* the fastest candidate of the exhaustive sweep */
+
+/* The configuration pjds_tune_pick chose. */
+typedef struct pjds_pick {
+  pjds_candidate cand; /* the chosen candidate as given in cands */
+  int32_t index;       /* its index in cands */
+  int32_t source;      /* PJDS_PICK_MODEL or PJDS_PICK_SWEEP */
+  double us;           /* its predicted (model) or measured (sweep) kernel time, microseconds */
+  int32_t n_outside;   /* features outside the model's range (> 0 sent the choice to the sweep) */
+  int32_t reserved;
+} pjds_pick;
+
+/*
+ * Choose the launch configuration of the product for a CRS matrix (host
+ * arrays) among n_cands candidates (e.g. pjds_tune_default_space for the
+ * caller's dtype). The features of the matrix are compared with the model's
+ * range, widened by 2% of its width on each side: inside it, the model
+ * predicts every candidate's time (CUDA inference kernel) and the smallest
+ * prediction wins; outside it, or with model = NULL, pjds_tune_sweep times
+ * every candidate (reps repetitions, L2 flushed through flush when given)
+ * and the fastest wins. work: device workspace of at least
+ * pjds_mlp_workspace_bytes(n_cands, 1) bytes (unused without a model).
+ * arena: the sweep's device arena (pjds_tune_arena_bytes), needed only when
+ * the sweep runs; NULL then returns PJDS_EINVAL. The result is written to
+ * *out: make a pJDS matrix with cand.b and cand.dtype and launch it with
+ * pjds_spmv_cfg and the candidate's fields. Synchronises the stream.
+ * Paper: Sect. 2.1 (the row-length distribution decides the format's
+ * benefit) and Sect. 4 (sliced ELLR-T, threads per row).
+ */
+int pjds_tune_pick(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx, const double *val,
+                   const pjds_mlp *model, const pjds_candidate *cands, int32_t n_cands, int32_t reps, void *work,
+                   size_t work_bytes, void *arena, size_t arena_bytes, void *flush, size_t flush_bytes,
+                   pjds_pick *out, void *stream);
 
 #ifdef __cplusplus
 }

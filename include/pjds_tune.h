@@ -35,6 +35,9 @@ typedef struct pjds_candidate {
   int32_t plan;            /* as in pjds_launch: 1 times the per-tile mapping of
                               the matrix's plan (the fields above then do not
                               apply); 0 with uniform fields set means -1 */
+  int32_t tile_order;      /* as in pjds_launch: 0 automatic, 1 the traversal
+                              table, -1 sorted order (uniform mappings) */
+  int32_t reserved;        /* 0 */
 } pjds_candidate;
 
 typedef struct pjds_tune_entry {
@@ -69,10 +72,12 @@ int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, cons
                     void *stream);
 
 /*
- * The default candidate space used by the tuners: b in {32, 64, 128, 256} x
- * threads per row in {1, 2, 4, 8} x the dtypes in dtype_mask (bit d set =
- * include pjds_dtype d), other fields 0. Writes at most max_out entries and
- * returns the count in *n_out.
+ * The candidate space of the tuners, for each dtype in dtype_mask (bit d set
+ * = include pjds_dtype d): b in {32, 64, 128, 256} x threads per row in
+ * {1, 2, 4, 8} x tile order in {sorted (-1), traversal table (1)}, then the
+ * per-tile mapping (plan = 1) for each b; 36 candidates per dtype, other
+ * fields 0 (their defaults). Writes at most max_out entries and returns the
+ * count in *n_out.
  */
 int pjds_tune_default_space(int32_t dtype_mask, pjds_candidate *out, int32_t max_out, int32_t *n_out);
 

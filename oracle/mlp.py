@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_H = 13, 64
+N_IN, N_H = 15, 64  # inputs: 8 matrix features + the 7-entry candidate encoding
 
 
 def init(seed: int = 0):

@@ -1,6 +1,8 @@
 // Cost model of the learned tuner (include/pjds_mlp.h): training and
-// inference kernels for a 13 -> 64 -> 64 -> 1 ReLU perceptron, the host
-// training loop, and the matrix features / candidate encoding.
+// inference kernels for a 15 -> 64 -> 64 -> 1 ReLU perceptron, the host
+// training loop, the matrix features / candidate encoding, and the choice of
+// a launch configuration (the model inside its feature range, the exhaustive
+// sweep outside it).
 //
 // One CTA of 256 threads handles 64 samples at a time with every parameter
 // and activation in shared memory (the model has 5121 parameters). W2 is kept
@@ -16,6 +18,7 @@
 
 #include "common.h"
 #include "pjds_mlp.h"
+#include "pjds_tune.h"
 
 namespace pjds {
 namespace mlp {
@@ -274,6 +277,25 @@ extern "C" int pjds_mlp_init(pjds_mlp *m, uint64_t seed) {
   for (float &w : m->w3) w = u(l2);
   for (int i = 0; i < IN; ++i) m->in_std[i] = 1.0f;
   m->out_std = 1.0f;
+  for (int i = 0; i < PJDS_MLP_FEATURES; ++i) {
+    m->feat_lo[i] = 1.0f;
+    m->feat_hi[i] = -1.0f;
+  }
+  return PJDS_OK;
+}
+
+extern "C" int pjds_mlp_fit_range(pjds_mlp *m, const float *feat, int32_t n) {
+  clear_error();
+  if (!m || !feat || n <= 0) return set_error(PJDS_EINVAL, "bad arguments");
+  for (int i = 0; i < PJDS_MLP_FEATURES; ++i) {
+    float lo = feat[i], hi = feat[i];
+    for (int64_t k = 1; k < n; ++k) {
+      lo = std::min(lo, feat[k * PJDS_MLP_FEATURES + i]);
+      hi = std::max(hi, feat[k * PJDS_MLP_FEATURES + i]);
+    }
+    m->feat_lo[i] = lo;
+    m->feat_hi[i] = hi;
+  }
   return PJDS_OK;
 }
 
@@ -440,12 +462,64 @@ extern "C" int pjds_tune_encode(const float feat[PJDS_MLP_FEATURES], const pjds_
   for (int32_t c = 0; c < n; ++c) {
     float *o = out + (int64_t)c * IN;
     for (int i = 0; i < PJDS_MLP_FEATURES; ++i) o[i] = feat[i];
-    const int32_t t = cands[c].threads_per_row > 0 ? cands[c].threads_per_row : 1;
+    const bool plan = cands[c].plan == 1;
+    const int32_t t = !plan && cands[c].threads_per_row > 0 ? cands[c].threads_per_row : 1;
     o[8] = (float)log2((double)cands[c].b / 32.0);
     o[9] = (float)log2((double)t);
     o[10] = cands[c].dtype == PJDS_F64 ? 1.0f : 0.0f;
     o[11] = cands[c].dtype == PJDS_F32 ? 1.0f : 0.0f;
     o[12] = cands[c].dtype == PJDS_BF16 ? 1.0f : 0.0f;
+    o[13] = plan ? 1.0f : 0.0f;
+    o[14] = !plan && cands[c].tile_order == 1 ? 1.0f : 0.0f;
   }
+  return PJDS_OK;
+}
+
+extern "C" int pjds_tune_pick(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
+                              const double *val, const pjds_mlp *model, const pjds_candidate *cands, int32_t n_cands,
+                              int32_t reps, void *work, size_t work_bytes, void *arena, size_t arena_bytes,
+                              void *flush, size_t flush_bytes, pjds_pick *out, void *stream) {
+  clear_error();
+  if (!out || !cands || n_cands <= 0 || !row_ptr || n_rows <= 0 || n_cols < 1)
+    return set_error(PJDS_EINVAL, "bad arguments");
+  memset(out, 0, sizeof(*out));
+  float feat[PJDS_MLP_FEATURES];
+  int rc = pjds_features(n_rows, n_cols, row_ptr, col_idx, feat);
+  if (rc) return rc;
+  int32_t outside = 0;
+  if (model) {
+    for (int i = 0; i < PJDS_MLP_FEATURES; ++i) {
+      const float lo = model->feat_lo[i], hi = model->feat_hi[i];
+      if (lo > hi) continue;  // no range: trusted
+      const float tol = 0.02f * (hi - lo);
+      outside += feat[i] < lo - tol || feat[i] > hi + tol;
+    }
+  }
+  out->n_outside = outside;
+  if (model && outside == 0) {
+    std::vector<float> X((size_t)n_cands * IN), pred((size_t)n_cands);
+    if ((rc = pjds_tune_encode(feat, cands, n_cands, X.data()))) return rc;
+    if ((rc = pjds_mlp_predict(model, X.data(), n_cands, pred.data(), work, work_bytes, stream))) return rc;
+    int32_t best = 0;
+    for (int32_t c = 1; c < n_cands; ++c)
+      if (pred[(size_t)c] < pred[(size_t)best]) best = c;
+    out->cand = cands[best];
+    out->index = best;
+    out->source = PJDS_PICK_MODEL;
+    out->us = exp((double)pred[(size_t)best]);
+    return PJDS_OK;
+  }
+  if (!arena) return set_error(PJDS_EINVAL, "the matrix lies outside the model's range and no sweep arena was given");
+  std::vector<pjds_tune_entry> e((size_t)n_cands);
+  int32_t best = -1;
+  rc = pjds_tune_sweep(n_rows, n_cols, row_ptr, col_idx, val, cands, n_cands, reps, arena, arena_bytes, flush,
+                       flush_bytes, e.data(), &best, stream);
+  if (rc) return rc;
+  if (best < 0) return set_error(PJDS_EINVAL, "no candidate ran");
+  out->cand = cands[best];
+  out->index = best;
+  out->source = PJDS_PICK_SWEEP;
+  out->us = e[(size_t)best].us;
+  clear_error();
   return PJDS_OK;
 }

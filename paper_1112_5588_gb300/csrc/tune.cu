@@ -81,21 +81,32 @@ extern "C" int pjds_tune_default_space(int32_t dtype_mask, pjds_candidate *out, 
   clear_error();
   if (!out || !n_out || max_out < 0) return set_error(PJDS_EINVAL, "bad arguments");
   int32_t n = 0;
-  const int32_t bs[4] = {32, 64, 128, 256}, ts[4] = {1, 2, 4, 8};
+  const int32_t bs[4] = {32, 64, 128, 256}, ts[4] = {1, 2, 4, 8}, os[2] = {-1, 1};
+  auto add = [&](const pjds_candidate &c) {
+    if (n < max_out) out[n] = c;
+    ++n;
+  };
   for (int32_t d = 0; d < 3; ++d) {
     if (!(dtype_mask & (1 << d))) continue;
     for (int32_t b : bs)
-      for (int32_t t : ts) {
-        if (n < max_out) {
+      for (int32_t t : ts)
+        for (int32_t o : os) {
           pjds_candidate c;
           memset(&c, 0, sizeof(c));
           c.b = b;
           c.dtype = d;
           c.threads_per_row = t;
-          out[n] = c;
+          c.tile_order = o;
+          add(c);
         }
-        ++n;
-      }
+    for (int32_t b : bs) {
+      pjds_candidate c;
+      memset(&c, 0, sizeof(c));
+      c.b = b;
+      c.dtype = d;
+      c.plan = 1;
+      add(c);
+    }
   }
   *n_out = std::min(n, max_out);
   return PJDS_OK;
@@ -190,6 +201,7 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
       in.block_threads = cands[i].block_threads;
       in.unroll = cands[i].unroll;
       in.plan = cands[i].plan;
+      in.tile_order = cands[i].plan == 1 ? 0 : cands[i].tile_order;
       const int r = pjds_spmv_resolve(&d, &in, &res);
       out[i].n_stored = n_stored;
       if (r != PJDS_OK) {
@@ -202,6 +214,7 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
       out[i].cand.unroll = res.unroll;
       out[i].cand.staged = res.staged;
       out[i].cand.plan = res.plan;
+      out[i].cand.tile_order = res.plan == 1 ? 0 : res.tile_order;
       std::vector<float> t((size_t)reps);
       int lr = PJDS_OK;
       for (int w = 0; w < 2 && lr == PJDS_OK; ++w) lr = pjds_spmv_cfg(&d, x, y, &res, stream);

@@ -17,7 +17,8 @@ DTYPE_NAMES = {0: "f64", 1: "f32", 2: "bf16"}
 
 class _Cand(ctypes.Structure):
     _fields_ = [("b", _i32), ("dtype", _i32), ("rows_per_thread", _i32), ("threads_per_row", _i32),
-                ("block_threads", _i32), ("unroll", _i32), ("staged", _i32), ("plan", _i32)]
+                ("block_threads", _i32), ("unroll", _i32), ("staged", _i32), ("plan", _i32), ("tile_order", _i32),
+                ("reserved", _i32)]
 
 
 class _Entry(ctypes.Structure):
@@ -36,23 +37,30 @@ for _name, _args in (("pjds_tune_arena_bytes", [_i32, _i32, _vp, _P(_Cand), _i32
 def _cand_dict(c) -> dict:
     return {"b": c.b, "dtype": DTYPE_NAMES.get(c.dtype, c.dtype), "rows_per_thread": c.rows_per_thread,
             "threads_per_row": c.threads_per_row, "block_threads": c.block_threads, "unroll": c.unroll,
-            "staged": c.staged, "plan": c.plan}
+            "staged": c.staged, "plan": c.plan, "tile_order": c.tile_order}
 
 
-def default_space(dtypes=("f64",), plan: bool = False) -> list:
-    """b in {32,64,128,256} x threads per row in {1,2,4,8} x dtypes; with
-    plan=True also the per-tile mapping for every b and dtype."""
+def default_space(dtypes=("f64",), plan: bool = True) -> list:
+    """The tuners' candidate space (pjds_tune_default_space): per dtype, b in
+    {32,64,128,256} x threads per row in {1,2,4,8} x tile order in {sorted,
+    table}, then the per-tile mapping for every b (36 per dtype); plan=False
+    leaves the per-tile mapping out."""
     mask = 0
     for d in dtypes:
         mask |= 1 << _p.DTYPES[d]
-    buf = (_Cand * 64)()
+    buf = (_Cand * 128)()
     n = _i32()
-    _p._check(_lib.pjds_tune_default_space(mask, buf, 64, ctypes.byref(n)), "pjds_tune_default_space")
+    _p._check(_lib.pjds_tune_default_space(mask, buf, 128, ctypes.byref(n)), "pjds_tune_default_space")
     out = [_cand_dict(buf[i]) for i in range(n.value)]
-    if plan:
-        out += [{"b": b, "dtype": d, "rows_per_thread": 0, "threads_per_row": 0, "block_threads": 0, "unroll": 0,
-                 "staged": 0, "plan": 1} for d in dtypes for b in (32, 64, 128, 256)]
-    return out
+    return out if plan else [c for c in out if c["plan"] != 1]
+
+
+def cand_key(c: dict) -> str:
+    """Short name of a candidate: b32_T1_sorted, b64_T2_table, b32_plan."""
+    if c.get("plan") == 1:
+        return f"b{c['b']}_plan"
+    order = {1: "table", -1: "sorted"}.get(c.get("tile_order", 0), "auto")
+    return f"b{c['b']}_T{c.get('threads_per_row', 0)}_{order}"
 
 
 def _to_cands(cands) -> ctypes.Array:
@@ -60,7 +68,7 @@ def _to_cands(cands) -> ctypes.Array:
     for i, c in enumerate(cands):
         arr[i] = _Cand(int(c["b"]), _p._dtype_code(c.get("dtype", "f64")), int(c.get("rows_per_thread", 0)),
                        int(c.get("threads_per_row", 0)), int(c.get("block_threads", 0)), int(c.get("unroll", 0)),
-                       int(c.get("staged", 0)), int(c.get("plan", 0)))
+                       int(c.get("staged", 0)), int(c.get("plan", 0)), int(c.get("tile_order", 0)), 0)
     return arr
 
 

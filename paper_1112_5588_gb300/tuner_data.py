@@ -10,16 +10,20 @@ Run on a GPU:
     python -m paper_1112_5588_gb300.tuner_data plan-eval timings.npz --rows test --out plan_test.npz
     python -m paper_1112_5588_gb300.tuner_data plan-fit plan_train.npz plan_test.npz      # CPU
 
-`generate` draws seeded synthetic matrices (N log-uniform, Zipf(s) row
-lengths with s uniform in [1.5, 3] and a cap drawn from {64, ..., 1024},
-columns uniform over the matrix or within a band), computes the features of
-each pattern and times the full candidate space (b in {32, 64, 128, 256} x
-threads per row in {1, 2, 4, 8} x {fp64, fp32, bf16}) with the exhaustive
-sweep. `train` fits the cost model (log of the kernel time) on the training
-matrices in libpjds's CUDA kernels. `evaluate` reports the regret of the
+`generate` draws seeded synthetic matrices (N log-uniform in [10k, 20M] by
+default, Zipf(s) row lengths with s uniform in [1.5, 3] and a cap drawn from
+{64, ..., 1024}, columns uniform over the matrix or within a band), computes
+the features of each pattern and times the full candidate space (b in {32,
+64, 128, 256} x threads per row in {1, 2, 4, 8} x tile order in {sorted,
+traversal table}, plus the per-tile mapping for each b, x {fp64, fp32, bf16}:
+108 candidates) with the exhaustive sweep. `train` fits the cost model (log of the kernel time) on the training
+matrices in libpjds's CUDA kernels and stores their feature range in the
+model (outside it pjds_tune_pick falls back to the sweep). `evaluate` reports the regret of the
 model's choice against the sweep's best on the held-out matrices, for each
-precision separately (the precision is the caller's choice; the tuner picks b
-and threads per row within it) and over all candidates. `recheck` rebuilds
+precision separately (the precision is the caller's choice; the tuner picks b,
+threads per row, tile order or the per-tile mapping within it) and over all
+candidates, beside the regret of the paper's fixed mapping and of the
+library's default mapping. `recheck` rebuilds
 the first `--count` held-out matrices from their stored parameters, times
 the candidate space again with the library as it is now, and reports the
 model's regret on those fresh timings and their agreement with the stored
@@ -59,19 +63,28 @@ def make_matrix(p: dict):
                            seed=p["seed"])
 
 
-def generate(n_train: int, n_test: int, seed: int = 2024, n_lo: float = 1e4, n_hi: float = 2e6, reps: int = 3,
-             log=sys.stderr) -> dict:
+def generate(n_train: int, n_test: int, seed: int = 2024, n_lo: float = 1e4, n_hi: float = 2e7, reps: int = 3,
+             log=sys.stderr, checkpoint: str | None = None) -> dict:
+    """Time the candidate space (tune.default_space: 36 candidates per
+    precision) on n_train + n_test synthetic matrices; with `checkpoint`, the
+    data gathered so far is saved there every 100 matrices."""
     from . import learned, tune
     cands = tune.default_space(DTYPES)
     n_all = n_train + n_test
     feats = np.zeros((n_all, 8), np.float32)
     times = np.full((n_all, len(cands)), np.nan, np.float64)
+    sizes = np.zeros((n_all, 3), np.int64)  # n_rows, nnz, longest row
     params = []
     t0 = time.time()
+
+    def pack(k):
+        return {"features": feats[:k], "times_us": times[:k], "sizes": sizes[:k], "n_train": min(n_train, k),
+                "cands": json.dumps(cands), "params": json.dumps(params[:k])}
     for i in range(n_all):
         p = matrix_params(i, seed if i < n_train else seed + 1, n_lo, n_hi)
         A = make_matrix(p)
         feats[i] = learned.features(A)
+        sizes[i] = (A.n_rows, A.nnz, int(np.diff(A.row_ptr).max()))
         entries, _ = tune.sweep(A, cands, reps=reps, flush_bytes=0)
         for c, e in enumerate(entries):
             if e["status"] == 0 and e["us"] > 0:
@@ -79,8 +92,31 @@ def generate(n_train: int, n_test: int, seed: int = 2024, n_lo: float = 1e4, n_h
         params.append(p)
         if (i + 1) % 50 == 0:
             print(f"[tuner_data] {i + 1}/{n_all} matrices, {time.time() - t0:.0f} s", file=log, flush=True)
-    return {"features": feats, "times_us": times, "n_train": n_train,
-            "cands": json.dumps(cands), "params": json.dumps(params)}
+        if checkpoint and (i + 1) % 100 == 0:
+            np.savez_compressed(checkpoint, **pack(i + 1))
+    return pack(n_all)
+
+
+def default_index(cands, n_rows: int, nnz: int, n_max: int, dtype: str) -> int:
+    """Index of the candidate pjds_spmv's default mapping runs for a matrix of
+    these sizes at b = 32 (include/pjds.h): the per-tile mapping when the
+    longest row exceeds 4 times the mean and n_rows reaches 2^16 / 2^17 / 2^18
+    (fp64 / fp32 / bf16), else the uniform threads per row with the traversal
+    table from 2^20 rows when the longest row is at most 4 times the mean."""
+    spread = n_max * n_rows > 4 * nnz
+    min_rows = {"f64": 1 << 16, "f32": 1 << 17, "bf16": 1 << 18}[dtype]
+    for k, c in enumerate(cands):
+        if c["dtype"] != dtype or c["b"] != 32:
+            continue
+        if spread and n_rows >= min_rows:
+            if c["plan"] == 1:
+                return k
+            continue
+        order = 1 if n_rows >= (1 << 20) and not spread else -1
+        if c["plan"] != 1 and c["threads_per_row"] == uniform_threads(n_rows, nnz, n_max, dtype) and \
+                c["tile_order"] == order:
+            return k
+    return -1
 
 
 def samples(data: dict, rows):
@@ -102,6 +138,7 @@ def train(data: dict, epochs: int = 400, batch: int = 1024, lr: float = 2e-3, se
     X, y = samples(data, range(n_train))
     m = learned.init(seed)
     learned.fit_scaling(m, X, y)
+    learned.fit_range(m, np.asarray(data["features"][:n_train], np.float32))
     hist = learned.train(m, X, y, epochs=epochs, batch=batch, lr=lr, seed=seed)
     return m, hist
 
@@ -117,8 +154,9 @@ def evaluate(data: dict, m) -> dict:
     groups.update({d: dt_of == k for k, d in enumerate(DTYPES)})
     rows = range(n_train, len(data["times_us"]))
     preds = {i: learned.predict(m, learned.encode(data["features"][i], cands)) for i in rows}
+    sizes = data.get("sizes")
     for name, sel in groups.items():
-        reg, default_reg = [], []
+        reg, paper_reg, lib_reg = [], [], []
         for i in rows:
             t = data["times_us"][i].copy()
             t[~sel] = np.nan
@@ -128,15 +166,22 @@ def evaluate(data: dict, m) -> dict:
             p[~(sel & np.isfinite(t))] = np.inf
             best = np.nanmin(t)
             reg.append(t[int(np.argmin(p))] / best - 1.0)
-            # the paper's mapping for comparison: b = 32, one thread per row
-            j0 = [c for c in range(len(cands)) if sel[c] and cands[c]["b"] == 32 and cands[c]["threads_per_row"] == 1]
+            # the paper's mapping for comparison: b = 32, one thread per row, sorted order
+            j0 = [c for c in range(len(cands)) if sel[c] and cands[c]["b"] == 32 and cands[c]["threads_per_row"] == 1
+                  and cands[c].get("plan", 0) != 1 and cands[c].get("tile_order", -1) in (0, -1)]
             if j0 and np.isfinite(t[j0[0]]):
-                default_reg.append(t[j0[0]] / best - 1.0)
+                paper_reg.append(t[j0[0]] / best - 1.0)
+            # the library's default mapping (pjds_spmv), when the sizes are stored
+            if sizes is not None and name in DTYPES:
+                k = default_index(cands, *[int(v) for v in sizes[i]], name)
+                if k >= 0 and np.isfinite(t[k]):
+                    lib_reg.append(t[k] / best - 1.0)
         reg = np.array(reg)
         out[name] = {"matrices": int(len(reg)), "mean_regret": float(reg.mean()),
                      "median_regret": float(np.median(reg)), "p90_regret": float(np.percentile(reg, 90)),
                      "within_5pct": float(np.mean(reg <= 0.05)),
-                     "paper_mapping_mean_regret": float(np.mean(default_reg)) if default_reg else None}
+                     "paper_mapping_mean_regret": float(np.mean(paper_reg)) if paper_reg else None,
+                     "library_default_mean_regret": float(np.mean(lib_reg)) if lib_reg else None}
     return out
 
 
@@ -253,8 +298,9 @@ def main(argv=None) -> int:
     g.add_argument("--n-test", type=int, default=200)
     g.add_argument("--seed", type=int, default=2024)
     g.add_argument("--n-lo", type=float, default=1e4)
-    g.add_argument("--n-hi", type=float, default=2e6)
+    g.add_argument("--n-hi", type=float, default=2e7)
     g.add_argument("--out", required=True)
+    g.add_argument("--checkpoint", default=None)
     t = sub.add_parser("train")
     t.add_argument("data")
     t.add_argument("--model", required=True)
@@ -277,7 +323,7 @@ def main(argv=None) -> int:
     pf.add_argument("test")
     a = ap.parse_args(argv)
     if a.cmd == "generate":
-        d = generate(a.n_train, a.n_test, a.seed, a.n_lo, a.n_hi)
+        d = generate(a.n_train, a.n_test, a.seed, a.n_lo, a.n_hi, checkpoint=a.checkpoint)
         np.savez_compressed(a.out, **d)
         print(json.dumps({"saved": a.out, "matrices": a.n_train + a.n_test}))
     elif a.cmd == "train":

@@ -16,14 +16,14 @@ def L():
 
 
 def _to_oracle(m):
-    return {"w1": np.array(m.w1, np.float64).reshape(64, 13), "b1": np.array(m.b1, np.float64),
+    return {"w1": np.array(m.w1, np.float64).reshape(64, 15), "b1": np.array(m.b1, np.float64),
             "w2": np.array(m.w2, np.float64).reshape(64, 64), "b2": np.array(m.b2, np.float64),
             "w3": np.array(m.w3, np.float64), "b3": np.array([m.b3], np.float64)}
 
 
 def _data(n, seed):
     rng = np.random.default_rng(seed)
-    X = rng.standard_normal((n, 13)).astype(np.float32)
+    X = rng.standard_normal((n, 15)).astype(np.float32)
     y = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] - X[:, 3]).astype(np.float32)
     return X, y
 

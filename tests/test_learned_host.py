@@ -32,17 +32,22 @@ def test_encode(L):
     cands = [{"b": 32, "dtype": "f64", "threads_per_row": 1}, {"b": 256, "dtype": "bf16", "threads_per_row": 8},
              {"b": 64, "dtype": "f32", "threads_per_row": 0}]
     X = L.encode(f, cands)
-    assert X.shape == (3, 13)
+    assert X.shape == (3, 15)
     assert np.array_equal(X[:, :8], np.tile(f, (3, 1)))
-    assert np.array_equal(X[:, 8:], [[0, 0, 1, 0, 0], [3, 3, 0, 0, 1], [1, 0, 0, 1, 0]])
+    assert np.array_equal(X[:, 8:], [[0, 0, 1, 0, 0, 0, 0], [3, 3, 0, 0, 1, 0, 0], [1, 0, 0, 1, 0, 0, 0]])
+    # the per-tile mapping (threads per row does not apply) and the traversal table
+    X = L.encode(f, [{"b": 64, "dtype": "f64", "plan": 1, "threads_per_row": 8, "tile_order": 1},
+                     {"b": 128, "dtype": "bf16", "threads_per_row": 2, "tile_order": 1},
+                     {"b": 128, "dtype": "bf16", "threads_per_row": 2, "tile_order": -1}])
+    assert np.array_equal(X[:, 8:], [[1, 0, 1, 0, 0, 1, 0], [2, 1, 0, 0, 1, 0, 1], [2, 1, 0, 0, 1, 0, 0]])
 
 
 def test_init_and_scaling(L):
     m = L.init(5)
     w1 = np.array(m.w1)
-    assert np.all(np.abs(w1) <= np.sqrt(6 / 13)) and w1.std() > 0.3
+    assert np.all(np.abs(w1) <= np.sqrt(6 / 15)) and w1.std() > 0.3
     assert np.array_equal(np.array(L.init(5).w2), np.array(m.w2))
-    X = np.random.default_rng(0).standard_normal((100, 13)).astype(np.float32) * 3 + 1
+    X = np.random.default_rng(0).standard_normal((100, 15)).astype(np.float32) * 3 + 1
     X[:, 4] = 2.0  # constant column keeps std 1
     y = np.random.default_rng(1).standard_normal(100).astype(np.float32)
     L.fit_scaling(m, X, y)
@@ -50,6 +55,15 @@ def test_init_and_scaling(L):
     assert np.allclose(np.array(m.in_std)[[0, 1, 2, 3, 5]], X.std(0)[[0, 1, 2, 3, 5]], rtol=1e-5)
     assert m.in_std[4] == 1.0
     assert m.out_mean == pytest.approx(y.mean(), abs=1e-6) and m.out_std == pytest.approx(y.std(), rel=1e-5)
+
+
+def test_feature_range(L):
+    m = L.init(3)
+    assert np.all(np.array(m.feat_lo) > np.array(m.feat_hi))  # none set
+    F = np.random.default_rng(2).standard_normal((50, 8)).astype(np.float32)
+    L.fit_range(m, F)
+    assert np.array_equal(np.array(m.feat_lo, np.float32), F.min(0))
+    assert np.array_equal(np.array(m.feat_hi, np.float32), F.max(0))
 
 
 def test_model_json_roundtrip(L, tmp_path):
@@ -65,11 +79,14 @@ def test_committed_model_and_data_are_consistent(L):
     import os
     here = os.path.dirname(L.MODEL_PATH)
     m = L.load()
-    assert len(m.w1) == 64 * 13 and len(m.w2) == 64 * 64 and m.out_std > 0
+    assert len(m.w1) == 64 * 15 and len(m.w2) == 64 * 64 and m.out_std > 0
     meta = json.load(open(L.MODEL_PATH))["meta"]
     for d in ("f64", "f32", "bf16"):
         assert meta["heldout"][d]["mean_regret"] <= 0.05
-    data = np.load(os.path.join(here, "data", "tuner_timings_gb300.npz"))
-    assert data["features"].shape == (2200, 8) and data["times_us"].shape == (2200, 48)
+    data = np.load(os.path.join(here, "data", "tuner_timings_full_gb300.npz"))
+    assert data["features"].shape == (2200, 8) and data["times_us"].shape == (2200, 108)
     assert int(data["n_train"]) == 2000
     assert np.isfinite(data["times_us"]).mean() > 0.99
+    # the model's feature range is the training matrices' range
+    F = data["features"][:2000]
+    assert np.allclose(np.array(m.feat_lo), F.min(0)) and np.allclose(np.array(m.feat_hi), F.max(0))

@@ -5,7 +5,7 @@ import pytest
 
 def _data(n, seed):
     rng = np.random.default_rng(seed)
-    X = rng.standard_normal((n, 13))
+    X = rng.standard_normal((n, 15))
     y = np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] - X[:, 3]
     return X, y
 
@@ -42,8 +42,8 @@ def test_adam_first_step_closed_form():
 def test_training_fits_a_linear_target():
     from oracle import mlp
     rng = np.random.default_rng(0)
-    X = rng.standard_normal((256, 13))
-    y = X @ rng.uniform(-1, 1, 13) + 0.3
+    X = rng.standard_normal((256, 15))
+    y = X @ rng.uniform(-1, 1, 15) + 0.3
     p, st = mlp.init(1), {}
     l0 = mlp.loss(p, X, y)
     for t in range(1, 1501):

@@ -16,11 +16,18 @@ def T():
 
 def test_default_space(T):
     s = T.default_space(("f64", "f32", "bf16"))
-    assert len(s) == 48
+    assert len(s) == 108
+    uni = [c for c in s if c["plan"] != 1]
     assert {c["b"] for c in s} == {32, 64, 128, 256}
-    assert {c["threads_per_row"] for c in s} == {1, 2, 4, 8}
+    assert {c["threads_per_row"] for c in uni} == {1, 2, 4, 8}
+    assert {c["tile_order"] for c in uni} == {-1, 1}
     assert {c["dtype"] for c in s} == {"f64", "f32", "bf16"}
-    assert len(T.default_space()) == 16
+    # every (b, threads per row, tile order) once per dtype, then the per-tile mapping for every b
+    for d in ("f64", "f32", "bf16"):
+        keys = [T.cand_key(c) for c in s if c["dtype"] == d]
+        assert len(keys) == len(set(keys)) == 36
+        assert sum(k.endswith("_plan") for k in keys) == 4
+    assert len(T.default_space()) == 36 and len(T.default_space(plan=False)) == 32
 
 
 @pytest.mark.parametrize("make", [lambda: synth.zipf_rows(20_000, s=1.8, len_max=400, seed=2),
