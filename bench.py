@@ -727,22 +727,36 @@ def batching_leg(torch, pjds, args, dev, flush):
     D = H.to_device(dev)
     H.destroy()
     spmm = {"matrix": f"DLR-like N={A.n_rows} nnz={A.nnz}", "dtype": "f32"}
+    peak = hbm_peak()[0]
     for k in (1, 4, 8, 16, 32):
         X = torch.rand(A.n_cols, k, device=dev)
         Y = torch.empty(A.n_rows, k, device=dev)
         t = statistics.median(time_launches(torch, lambda: batch.spmm(D, X, Y), 10, 3, flush))
         nb = A.nnz * 8 + 4 * k * (A.n_cols + A.n_rows) + 4 * A.n_rows
         spmm[f"k{k}"] = {"us": round(t * 1e6, 2), "gbs": round(nb / t / 1e9, 1),
+                         "frac_of_hbm": round(nb / t / 1e9 / peak, 4),
                          "gflops": round(2 * A.nnz * k / t / 1e9, 1),
                          "us_per_rhs": round(t * 1e6 / k, 2)}
+        # the gather ceiling: the same launch without the value stream (k rows of X
+        # gathered per entry, 4 k bytes each, through L1/L2)
+        if k == 1:
+            tp = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv_pattern(D, X.view(-1), Y.view(-1)),
+                                                 10, 3, flush))
+        else:
+            tp = statistics.median(time_launches(torch, lambda: batch.spmm_pattern(D, X, Y), 10, 3, flush))
+        spmm[f"k{k}"]["gather_ceiling_us"] = round(tp * 1e6, 2)
+        spmm[f"k{k}"]["frac_of_gather_ceiling"] = round(tp / t, 4)
+        spmm[f"k{k}"]["gathered_bytes_per_entry"] = 4 * k
+    spmm["ceiling_note"] = ("frac_of_gather_ceiling = pattern-product time / product time: the pattern product "
+                            "(pjds_spmm_pattern) is the same launch without reading the values")
     out["spmm"] = spmm
     del D
     rng = np.random.default_rng(args.seed)
     sizes = np.exp(rng.uniform(np.log(10_000), np.log(500_000), 64)).astype(int)
     from paper_1112_5588_gb300 import learned
     model = learned.load()
-    cands = [{"b": 32, "dtype": "f64", "rows_per_thread": 0, "threads_per_row": t, "block_threads": 0, "unroll": 0}
-             for t in (1, 2, 4, 8)]
+    cands = [{"b": 32, "dtype": "f64", "rows_per_thread": 0, "threads_per_row": t, "block_threads": 0, "unroll": 0,
+              "tile_order": -1} for t in (1, 2, 4, 8)]
     devs, xs, ys, nnz, nbytes, tuned = [], [], [], 0, 0, []
     for m, n in enumerate(sizes):
         M = synth.zipf_rows(int(n), s=2.0, len_max=512, seed=args.seed + m)
@@ -800,29 +814,36 @@ def batching_leg(torch, pjds, args, dev, flush):
 
 
 def tuning_leg(torch, pjds, args, dev):
-    """The threads-per-row / b sweep on the DLR-like matrix (long rows, fp32):
-    the exhaustive autotuner's 16 candidates (b in 32..256, T in 1..8) with
-    the L2 flushed between runs, against the paper's mapping (b = 32, one
-    thread per row), the library's default and the learned tuner's pick."""
+    """The candidate sweep on the DLR-like matrix (long rows, fp32): the
+    exhaustive autotuner's 36 candidates (b in 32..256, T in 1..8, sorted or
+    table tile order, the per-tile mapping) with the L2 flushed between runs,
+    against the paper's mapping (b = 32, one thread per row), the library's
+    default and the learned picker (pjds_tune_pick: the model inside its
+    training range, the sweep outside it)."""
     import synth
-    from paper_1112_5588_gb300 import learned, tune
+    from paper_1112_5588_gb300 import learned, tune, tuner_data
     A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=args.seed)
     cands = tune.default_space(("f32",))
     entries, best = tune.sweep(A, cands, reps=5)
-    us = {f"b{e['b']}_T{e['threads_per_row']}": round(e["us"], 2) for e in entries if e["status"] == 0}
-    paper = us["b32_T1"]
-    pick = learned.choose(A, cands)[1]
-    t_pick = us[f"b{pick['b']}_T{pick['threads_per_row']}"]
+    us = {tune.cand_key(c): round(e["us"], 2) for c, e in zip(cands, entries) if e["status"] == 0}
+    paper = us["b32_T1_sorted"]
+    pick = learned.pick(A, "f32")
+    t_pick = us[tune.cand_key(pick)]
     D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f32").to_device(dev)
     x = torch.rand(A.n_cols, device=dev)
     y = torch.empty(A.n_rows, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     t_def = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 10, 3, flush)) * 1e6
-    best_key = f"b{entries[best]['b']}_T{entries[best]['threads_per_row']}"
+    k_def = tuner_data.default_index(cands, A.n_rows, A.nnz, int(np.diff(A.row_ptr).max()), "f32")
+    best_key = tune.cand_key(cands[best])
     return {"matrix": f"DLR-like N={A.n_rows} nnz={A.nnz} (144/row), fp32", "sweep_us": us,
             "best": best_key, "best_us": us[best_key], "paper_mapping_us": paper,
             "default_mapping": pjds.pjds_spmv_resolve(D), "default_us": round(t_def, 2),
-            "learned_pick": f"b{pick['b']}_T{pick['threads_per_row']}", "learned_pick_us": t_pick,
+            "default_in_sweep": tune.cand_key(cands[k_def]) if k_def >= 0 else None,
+            "default_regret_in_sweep": round(us[tune.cand_key(cands[k_def])] / us[best_key] - 1, 4)
+            if k_def >= 0 else None,
+            "picker": {"choice": tune.cand_key(pick), "source": pick["source"], "features_outside": pick["n_outside"],
+                       "us": t_pick, "live_regret": round(t_pick / us[best_key] - 1, 4)},
             "best_speedup_over_paper_mapping": round(paper / us[best_key], 3)}
 
 
@@ -830,9 +851,11 @@ def spread_leg(torch, pjds, args, dev, flush):
     """Widely spread row lengths (sAMG-like: Zipf s = 2, rows of 1 to 512
     entries, 1M rows; fp64 and fp32): the per-tile mapping pjds_spmv takes
     for such a matrix against every uniform threads-per-row count, L2 flushed
-    before each launch."""
+    before each launch; and the learned picker's choice against the
+    exhaustive sweep of the candidate space."""
     med = statistics.median
     import synth
+    from paper_1112_5588_gb300 import learned, tune, tuner_data
     A = synth.zipf_rows(1_000_000, s=2.0, len_max=512, seed=args.seed)
     lens = np.diff(A.row_ptr)
     out = {"matrix": f"Zipf s=2 N={A.n_rows} nnz={A.nnz} (rows up to {int(lens.max())}, mean {lens.mean():.2f})"}
@@ -845,13 +868,30 @@ def spread_leg(torch, pjds, args, dev, flush):
         y = torch.empty(A.n_rows, dtype=D.vec_dtype, device=dev)
         nb = alg_bytes(A.n_rows, A.n_cols, A.nnz, vb, xb)
         t_def = med(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 20, 3, flush))
+        t_hot = med(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 20, 3, None))
         uni = {t: med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, x, y, threads_per_row=t, plan=-1), 20, 3, flush))
                for t in (1, 2, 4, 8)}
         best = min(uni, key=uni.get)
         out[dt] = {"default_uses_plan": pjds.pjds_spmv_resolve(D)["plan"] == 1, "plan_tiles": n_plan,
                    "default_us": round(t_def * 1e6, 2), "default_gbs": round(nb / t_def / 1e9, 1),
+                   "working_set_mb": round(nb / 1e6, 1), "l2_mb": 129,
+                   "default_l2_warm_us": round(t_hot * 1e6, 2),
+                   "bound": ("L2-resident working set: measured cold (L2 flushed before each launch) and warm; "
+                             "a warm time near the cold one means latency, not DRAM, sets it"),
                    "uniform_us": {f"T{t}": round(v * 1e6, 2) for t, v in uni.items()},
                    "best_uniform": f"T{best}", "speedup_vs_best_uniform": round(uni[best] / t_def, 3)}
+        # the learned picker against the exhaustive sweep of the 36 candidates (one sweep, L2 flushed)
+        cands = tune.default_space((dt,))
+        entries, k_best = tune.sweep(A, cands, reps=5)
+        pick = learned.pick(A, dt)
+        k_def = tuner_data.default_index(cands, A.n_rows, A.nnz, int(lens.max()), dt)
+        t_best = entries[k_best]["us"]
+        out[dt]["sweep_best"] = tune.cand_key(cands[k_best])
+        out[dt]["sweep_best_us"] = round(t_best, 2)
+        out[dt]["picker"] = {"choice": tune.cand_key(pick), "source": pick["source"],
+                             "us": round(entries[pick["index"]]["us"], 2),
+                             "live_regret": round(entries[pick["index"]]["us"] / t_best - 1, 4)}
+        out[dt]["default_regret_in_sweep"] = round(entries[k_def]["us"] / t_best - 1, 4) if k_def >= 0 else None
         del D, x, y
     torch.cuda.synchronize()
     return out

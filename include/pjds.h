@@ -157,7 +157,22 @@ typedef struct pjds_dev {
 int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
                 const double *val, int32_t b, int32_t dtype, int32_t permute_cols, pjds_host **out);
 
-/* Free a handle from pjds_create (NULL is accepted). */
+/*
+ * The structure of the pJDS matrix from the row lengths alone (row_ptr[n_rows
+ * + 1]): the sort, padding, jagged-diagonal offsets, traversal table and
+ * per-tile plan of pjds_create (original basis), every array equal to
+ * pjds_create's for any columns and values with these row lengths, but col
+ * and val are left NULL: the caller fills the n_stored entries itself (entry
+ * j of sorted row i, perm[i] being its original row, at col_start[j] + i for
+ * j < row_len[i]; pads, up to the block length, column -1 and value +0), for
+ * example directly in device memory when the CRS arrays would not fit the
+ * host. Nothing checks those entries. The paper has no counterpart of this
+ * call. Errors as pjds_create; free with pjds_destroy.
+ */
+int pjds_create_shape(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, int32_t b, int32_t dtype,
+                      pjds_host **out);
+
+/* Free a handle from pjds_create or pjds_create_shape (NULL is accepted). */
 int pjds_destroy(pjds_host *h);
 
 /*

@@ -36,6 +36,18 @@ extern "C" {
  */
 int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream);
 
+/*
+ * Pattern product Y = S X for k >= 2 right-hand sides, S the sparsity pattern
+ * of A (every stored entry taken as 1): the launch pjds_spmm makes, without
+ * reading val, each column summed in order with plain additions. Its time is
+ * a floor for pjds_spmm's on the same matrix and k: the gathered rows of X
+ * (4 k or 8 k bytes per entry), the column stream and the stores of Y, the
+ * gather ceiling the block product is measured against. Same arguments and
+ * errors as pjds_spmm; k = 1 returns PJDS_EINVAL (use pjds_spmv_pattern).
+ * The paper has no counterpart of this call.
+ */
+int pjds_spmm_pattern(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream);
+
 /* Opaque host handle of a batch plan. */
 typedef struct pjds_batch pjds_batch;
 

@@ -13,6 +13,7 @@ _i32, _vp, _sz = ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
 _P = ctypes.POINTER
 for _name, _res, _args in (
         ("pjds_spmm", ctypes.c_int, [_P(_p._PjdsDevS), _i32, _vp, _vp, _vp]),
+        ("pjds_spmm_pattern", ctypes.c_int, [_P(_p._PjdsDevS), _i32, _vp, _vp, _vp]),
         ("pjds_batch_plan_bytes", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_sz)]),
         ("pjds_batch_create", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_vp), _P(_vp), _vp, _sz, _P(_vp), _vp]),
         ("pjds_batch_create_lanes", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_vp), _P(_vp), _P(_i32), _vp, _sz,
@@ -28,8 +29,7 @@ for _name, _res, _args in (
     getattr(_lib, _name).argtypes = _args
 
 
-def spmm(A, X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
-    """Y = A X (pjds_spmm); X: (n_cols, k), Y: (n_rows, k), row-major, A's vector type."""
+def _spmm_call(fn, name, A, X, Y, stream):
     if X.dim() != 2 or Y.dim() != 2 or X.shape[1] != Y.shape[1]:
         raise ValueError("X and Y must be 2-D with the same number of columns")
     k = X.shape[1]
@@ -37,9 +37,19 @@ def spmm(A, X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
     _p._check_vec(Y.reshape(-1), A.n_rows * k, A.vec_dtype, "Y")
     if not (X.is_contiguous() and Y.is_contiguous()):
         raise ValueError("X and Y must be contiguous (row-major)")
-    _p._check(_lib.pjds_spmm(ctypes.byref(A.struct), k, X.data_ptr(), Y.data_ptr(), _p._stream_ptr(stream)),
-              "pjds_spmm")
+    _p._check(fn(ctypes.byref(A.struct), k, X.data_ptr(), Y.data_ptr(), _p._stream_ptr(stream)), name)
     return Y
+
+
+def spmm(A, X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
+    """Y = A X (pjds_spmm); X: (n_cols, k), Y: (n_rows, k), row-major, A's vector type."""
+    return _spmm_call(_lib.pjds_spmm, "pjds_spmm", A, X, Y, stream)
+
+
+def spmm_pattern(A, X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
+    """Y = S X, S the sparsity pattern of A (pjds_spmm_pattern): the launch of
+    spmm without the value stream, its gather ceiling."""
+    return _spmm_call(_lib.pjds_spmm_pattern, "pjds_spmm_pattern", A, X, Y, stream)
 
 
 class Batch:

@@ -48,7 +48,9 @@ struct V16<double> {
 // per row). Wider lanes spread the loads of col_start, col and val and the
 // address arithmetic over more fused multiply-adds. Row offsets into X and Y
 // are 32-bit indices widened in the multiply (one wide multiply-add each).
-template <typename TV, typename TX, typename IDX, bool SCATTER, int CH>
+// PAT: the pattern product Y = S X (every stored value taken as 1, val not
+// read): the same column stream, X-row gathers and Y stores, plain additions.
+template <typename TV, typename TX, typename IDX, bool SCATTER, int CH, bool PAT = false>
 __global__ void __launch_bounds__(BT)
     spmm_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ col_start,
                 const int32_t *__restrict__ block_len, const int32_t *__restrict__ perm, const TX *__restrict__ X,
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(BT)
         }
 #endif
         c[u] = __ldcs(col + o);
-        v[u] = dev::ld_stream1(val + o);
+        if constexpr (!PAT) v[u] = dev::ld_stream1(val + o);
       } else {
         c[u] = -1;
         v[u] = TV{};
@@ -100,8 +102,12 @@ __global__ void __launch_bounds__(BT)
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int w = 0; w < W; ++w)
-        acc[w] = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u][w], acc[w]) : acc[w];
+      for (int w = 0; w < W; ++w) {
+        if constexpr (PAT)
+          acc[w] = c[u] >= 0 ? acc[w] + (TA)xv[u][w] : acc[w];
+        else
+          acc[w] = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u][w], acc[w]) : acc[w];
+      }
   }
   TX out[W];
 #pragma unroll
@@ -200,7 +206,7 @@ static int spmm_chunks(const pjds_dev *A, int32_t k, int vw) {
   return lanes >= 2 && (int64_t)A->n_rows * lanes >= (1 << 19) ? 2 : 1;
 }
 
-template <typename TV, typename TX>
+template <typename TV, typename TX, bool PAT = false>
 static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cudaStream_t s) {
   constexpr int VW = V16<TX>::W;
   const int ch = spmm_chunks(A, k, VW);
@@ -217,7 +223,8 @@ static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cud
   dev::set_extents(dev::Extents{A->n_stored, A->n_cols, A->n_rows, A->n_blocks, A->n_max + 1}, s);
 #endif
 #define SPMM(IDX, SC, CH)                                                                                        \
-  spmm_kernel<TV, TX, IDX, SC, CH><<<(unsigned)grid, BT, 0, s>>>(val, A->col, A->col_start, A->block_len, A->perm, \
+  spmm_kernel<TV, TX, IDX, SC, CH, PAT><<<(unsigned)grid, BT, 0, s>>>(val, A->col, A->col_start, A->block_len,    \
+                                                                       A->perm, \
                                                                   x, y, A->n_rows, A->b, k, lr)
 #define SPMM_CH(IDX, SC) \
   do {                   \
@@ -239,11 +246,13 @@ static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cud
   return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "pjds_spmm launch: %s", cudaGetErrorString(e));
 }
 
-extern "C" int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream) {
+template <bool PAT>
+static int spmm_entry(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream) {
   clear_error();
   if (!A) return set_error(PJDS_EINVAL, "A is NULL");
   if (value_bytes(A->dtype) == 0) return set_error(PJDS_EINVAL, "unknown dtype %d", A->dtype);
-  if (k == 1) return pjds_spmv(A, X, Y, stream);
+  if (k == 1 && !PAT) return pjds_spmv(A, X, Y, stream);
+  if (k == 1) return set_error(PJDS_EINVAL, "k = 1: use pjds_spmv_pattern");
   const int w = A->dtype == PJDS_F64 ? 2 : 4;
   if (k < w || k % w || k > 32 * w)
     return set_error(PJDS_EINVAL, "k = %d: use 1 or a multiple of %d up to %d", k, w, 32 * w);
@@ -262,10 +271,18 @@ extern "C" int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, v
     return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
   switch (A->dtype) {
-    case PJDS_F64: return launch_spmm<double, double>(A, k, X, Y, s);
-    case PJDS_F32: return launch_spmm<float, float>(A, k, X, Y, s);
-    default: return launch_spmm<dev::bf16_t, float>(A, k, X, Y, s);
+    case PJDS_F64: return launch_spmm<double, double, PAT>(A, k, X, Y, s);
+    case PJDS_F32: return launch_spmm<float, float, PAT>(A, k, X, Y, s);
+    default: return launch_spmm<dev::bf16_t, float, PAT>(A, k, X, Y, s);
   }
+}
+
+extern "C" int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream) {
+  return spmm_entry<false>(A, k, X, Y, stream);
+}
+
+extern "C" int pjds_spmm_pattern(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream) {
+  return spmm_entry<true>(A, k, X, Y, stream);
 }
 
 // ----------------------------------------------------------------------------- batch

@@ -79,13 +79,13 @@ static void clear_values(void *dst, int64_t o, int64_t n, int32_t dtype) {
 
 // Shared CRS validation; fills len[i].
 static int check_crs(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
-                     const double *val, int32_t dtype, std::vector<int32_t> &len) {
+                     const double *val, int32_t dtype, std::vector<int32_t> &len, bool entries = true) {
   if (n_rows < 0 || n_cols < 1) return set_error(PJDS_EINVAL, "n_rows must be >= 0 and n_cols >= 1");
   if (!row_ptr) return set_error(PJDS_EINVAL, "row_ptr is NULL");
   if (value_bytes(dtype) == 0) return set_error(PJDS_EINVAL, "unknown dtype %d", dtype);
   if (row_ptr[0] != 0) return set_error(PJDS_EINVAL, "row_ptr[0] must be 0");
   const int64_t nnz = row_ptr[n_rows];
-  if (nnz > 0 && (!col_idx || !val)) return set_error(PJDS_EINVAL, "col_idx/val is NULL");
+  if (entries && nnz > 0 && (!col_idx || !val)) return set_error(PJDS_EINVAL, "col_idx/val is NULL");
   len.resize((size_t)n_rows);
   for (int32_t i = 0; i < n_rows; ++i) {
     const int64_t l = row_ptr[i + 1] - row_ptr[i];
@@ -93,6 +93,7 @@ static int check_crs(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, con
     if (l > std::numeric_limits<int32_t>::max()) return set_error(PJDS_EOVERFLOW, "row %d too long", i);
     len[i] = (int32_t)l;
   }
+  if (!entries) return PJDS_OK;
   int bad = 0;
 #pragma omp parallel for schedule(static) reduction(| : bad)
   for (int64_t k = 0; k < nnz; ++k) bad |= (col_idx[k] < 0 || col_idx[k] >= n_cols);
@@ -143,15 +144,17 @@ extern "C" void pjds_abi_sizes(int32_t out[5]) {
   out[4] = (int32_t)sizeof(ellr_dev);
 }
 
-extern "C" int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
-                           const double *val, int32_t b, int32_t dtype, int32_t permute_cols, pjds_host **out) {
-  clear_error();
+// pjds_create (fill = true) and pjds_create_shape (fill = false: the
+// structure from the row lengths alone, col and val left NULL).
+static int create_impl(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
+                       const double *val, int32_t b, int32_t dtype, int32_t permute_cols, bool fill,
+                       pjds_host **out) {
   if (!out) return set_error(PJDS_EINVAL, "out is NULL");
   *out = nullptr;
   if (b <= 0 || b % 32 != 0) return set_error(PJDS_EINVAL, "b = %d is not a positive multiple of 32", b);
   if (permute_cols && n_rows != n_cols) return set_error(PJDS_EINVAL, "permute_cols needs a square matrix");
   std::vector<int32_t> len;
-  int rc = check_crs(n_rows, n_cols, row_ptr, col_idx, val, dtype, len);
+  int rc = check_crs(n_rows, n_cols, row_ptr, col_idx, val, dtype, len, fill);
   if (rc) return rc;
 
   const int64_t n_pad64 = ((int64_t)n_rows + b - 1) / b * b;
@@ -208,21 +211,24 @@ extern "C" int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_pt
     free_pjds(h);
     return set_error(PJDS_EOVERFLOW, "stored element count too large");
   }
-  h->col = alloc_n<int32_t>(h->n_stored);
-  h->val = malloc((size_t)std::max<int64_t>(h->n_stored, 1) * value_bytes(dtype));
-  if (!h->col || !h->val) {
-    free_pjds(h);
-    return set_error(PJDS_ENOMEM, "out of host memory (%lld stored elements)", (long long)h->n_stored);
+  const int32_t *perm = h->perm;
+  if (fill) {
+    h->col = alloc_n<int32_t>(h->n_stored);
+    h->val = malloc((size_t)std::max<int64_t>(h->n_stored, 1) * value_bytes(dtype));
+    if (!h->col || !h->val) {
+      free_pjds(h);
+      return set_error(PJDS_ENOMEM, "out of host memory (%lld stored elements)", (long long)h->n_stored);
+    }
   }
 
   // fill: sorted row i, entry j -> col_start[j] + i; padding up to the block length
   const int64_t *cs = h->col_start;
-  const int32_t *perm = h->perm, *inv = h->inv_perm, *rl = h->row_len, *bl = h->block_len;
+  const int32_t *inv = h->inv_perm, *rl = h->row_len, *bl = h->block_len;
   int32_t *col = h->col;
   void *v = h->val;
   const int permc = h->permute_cols;
-#pragma omp parallel for schedule(static, 4096)
-  for (int64_t i = 0; i < n_pad; ++i) {
+#pragma omp parallel for schedule(static, 4096) if (fill)
+  for (int64_t i = 0; i < (fill ? n_pad : 0); ++i) {
     const int32_t L = bl[i / b], li = rl[i];
     if (li > 0) {
       const int64_t src = row_ptr[perm[i]];
@@ -281,6 +287,18 @@ extern "C" int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_pt
   }
   *out = h;
   return PJDS_OK;
+}
+
+extern "C" int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const int32_t *col_idx,
+                           const double *val, int32_t b, int32_t dtype, int32_t permute_cols, pjds_host **out) {
+  clear_error();
+  return create_impl(n_rows, n_cols, row_ptr, col_idx, val, b, dtype, permute_cols, true, out);
+}
+
+extern "C" int pjds_create_shape(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, int32_t b, int32_t dtype,
+                                 pjds_host **out) {
+  clear_error();
+  return create_impl(n_rows, n_cols, row_ptr, nullptr, nullptr, b, dtype, 0, false, out);
 }
 
 extern "C" int pjds_destroy(pjds_host *h) {

@@ -81,6 +81,7 @@ def _load_lib():
         "pjds_version": (_i32, []),
         "pjds_abi_sizes": (None, [_vp]),
         "pjds_create": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _i32, P(P(_PjdsHostS))]),
+        "pjds_create_shape": (ctypes.c_int, [_i32, _i32, _vp, _i32, _i32, P(P(_PjdsHostS))]),
         "pjds_destroy": (ctypes.c_int, [P(_PjdsHostS)]),
         "pjds_spmv": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, _vp]),
         "pjds_spmv_cfg": (ctypes.c_int, [P(_PjdsDevS), _vp, _vp, P(_LaunchS), _vp]),
@@ -214,10 +215,26 @@ def pjds_create(n_rows: int, n_cols: int, row_ptr, col, val, b: int = 32, dtype=
     return PjdsHost(out)
 
 
-class PjdsDevice:
-    """Device copy of a pJDS matrix in torch-owned buffers plus its pjds_dev struct."""
+def pjds_create_shape(n_rows: int, n_cols: int, row_ptr, b: int = 32, dtype="f64") -> PjdsHost:
+    """The pJDS structure from the row lengths alone (pjds_create_shape):
+    col and val are empty; PjdsDevice(host, col=..., val=...) takes them as
+    caller-filled device tensors."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    if len(rp) != n_rows + 1:
+        raise ValueError("row_ptr must have n_rows + 1 entries")
+    out = ctypes.POINTER(_PjdsHostS)()
+    _check(_lib.pjds_create_shape(n_rows, n_cols, rp.ctypes.data, b, _dtype_code(dtype), ctypes.byref(out)),
+           "pjds_create_shape")
+    return PjdsHost(out)
 
-    def __init__(self, host: PjdsHost, device="cuda", tile_order: bool = True, plan: bool = True):
+
+class PjdsDevice:
+    """Device copy of a pJDS matrix in torch-owned buffers plus its pjds_dev
+    struct. col / val: device tensors of n_stored entries (int32, and the
+    value type; bf16 as int16 bits) to use instead of uploading the host's."""
+
+    def __init__(self, host: PjdsHost, device="cuda", tile_order: bool = True, plan: bool = True,
+                 col: torch.Tensor | None = None, val: torch.Tensor | None = None):
         dev = torch.device(device)
         self.device = dev
         self.dtype = host.dtype
@@ -233,8 +250,15 @@ class PjdsDevice:
         self.block_len = up(host.block_len, np.int32)
         self.row_len = up(host.row_len, np.int32)
         self.col_start = up(host.col_start, np.int64)
-        self.col = up(host.col, np.int32)
-        self.val = up(host.val, {0: np.float64, 1: np.float32, 2: np.int16}[host.dtype])
+        if col is not None or val is not None:
+            vt = {0: torch.float64, 1: torch.float32, 2: torch.int16}[host.dtype]
+            for t, n, dt, nm in ((col, host.n_stored, torch.int32, "col"), (val, host.n_stored, vt, "val")):
+                if t is None or t.device.type != "cuda" or t.dtype != dt or t.numel() != n or not t.is_contiguous():
+                    raise ValueError(f"{nm} must be a contiguous CUDA {dt} tensor with {n} elements")
+            self.col, self.val = col, val
+        else:
+            self.col = up(host.col, np.int32)
+            self.val = up(host.val, {0: np.float64, 1: np.float32, 2: np.int16}[host.dtype])
         self.tile_order = up(host.tile_order, np.int32) if tile_order else None
         self.n_plan = host.n_plan if plan else 0
         self.plan = up(host.plan, np.int32) if plan and host.n_plan > 0 else None

@@ -42,6 +42,25 @@ def test_library_exports_every_declared_symbol(P):
     assert missing == []
 
 
+@pytest.mark.parametrize("b", [32, 64])
+def test_create_shape_equals_create(P, b):
+    # the structure from the row lengths alone is pjds_create's, without col / val
+    for A in (synth.hmep_like(n=20_000, seed=3), tiny.random_lengths(1037, 900, max_len=70, seed=5, p_empty=0.2),
+              synth.zipf_rows(70_000, s=2.0, len_max=512, seed=2), tiny.from_lengths([0] * 40, 7)):
+        for dt in ("f64", "bf16"):
+            H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b, dtype=dt)
+            S = P.pjds_create_shape(A.n_rows, A.n_cols, A.row_ptr, b=b, dtype=dt)
+            for k in ("n_rows", "n_cols", "n_pad", "b", "n_blocks", "n_max", "nnz", "n_stored", "dtype", "n_plan"):
+                assert getattr(S, k) == getattr(H, k), k
+            for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "tile_order", "plan"):
+                assert np.array_equal(getattr(S, k), getattr(H, k)), k
+            assert len(S.col) == 0 and len(S.val) == 0
+            H.destroy()
+            S.destroy()
+    with pytest.raises(P.PjdsError):
+        P.pjds_create_shape(3, 3, np.array([0, 2, 1, 4]), b=32)  # row_ptr decreases
+
+
 def test_abi_version_and_struct_sizes(P):
     assert P.lib().pjds_version() == 4  # the binding itself checked the struct sizes on load
 

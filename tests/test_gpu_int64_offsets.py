@@ -10,8 +10,11 @@ fp32 accumulation of the bf16 kernels is exact, and sampled rows must equal
 the fp64 oracle bit for bit. Rows and columns come from closed formulas, so
 the oracle evaluates the sampled rows without the full matrix.
 
-Needs about 50 GB of free host memory and 32 GB of free device memory;
-skipped otherwise.
+The matrix never exists on the host: pjds_create_shape gives the pJDS
+structure from the row lengths (2^24 + 1 offsets), and the test fills col
+and val in device memory one jagged diagonal at a time from the same
+formulas; ELLPACK-R is filled on the device the same way. About 28 GB of
+device memory and a few hundred MB of host memory.
 """
 import numpy as np
 import pytest
@@ -22,6 +25,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 N = 1 << 24
 STRIDE = 4099  # column step between a row's entries; 132 * 4099 < N keeps them distinct
+N_MAX = 132
 
 
 def _lengths(r):
@@ -43,25 +47,35 @@ def _x():
     return ((((j * 11) % 17) - 8) / 16.0).astype(np.float32)
 
 
-def _mem_available_gb():
-    try:
-        with open("/proc/meminfo") as fh:
-            for line in fh:
-                if line.startswith("MemAvailable:"):
-                    return int(line.split()[1]) / 1e6
-    except OSError:
-        pass
-    return 0.0
+def _diagonal(torch, r, j):
+    """Entry j of original rows r (int64 device tensor): (column, bf16 bits), pads (-1, +0)."""
+    live = j < _lengths(r)
+    c = torch.where(live, (r + j * STRIDE) % N, torch.full_like(r, -1)).to(torch.int32)
+    v = torch.where(live, (((r * 3 + j * 5) % 15) - 7).to(torch.float32) * 0.125, torch.zeros((), device=r.device))
+    return c, v.to(torch.bfloat16).view(torch.int16)
+
+
+class _EllrView:
+    """The few attributes ellr_spmv reads, over caller-filled device arrays."""
+
+    def __init__(self, P, torch, row_max, col, val, nnz):
+        self.n_rows = self.n_cols = self.n_pad = N
+        self.n_max = N_MAX
+        self.vec_dtype = torch.float32
+        self._keep = (row_max, col, val)
+        s = P._EllrDevS()
+        s.n_rows, s.n_cols, s.n_pad, s.n_max = N, N, N, N_MAX
+        s.nnz, s.n_stored, s.dtype = nnz, N * N_MAX, 2
+        s.row_max, s.col, s.val = row_max.data_ptr(), col.data_ptr(), val.data_ptr()
+        self.struct = s
 
 
 @pytest.fixture(scope="module")
 def big():
     import torch
     assert torch.cuda.is_available(), "GPU tests need CUDA"
-    if _mem_available_gb() < 80:
-        pytest.skip("needs about 50 GB of free host memory")
-    if torch.cuda.mem_get_info()[0] < 48e9:
-        pytest.skip("needs about 32 GB of free device memory")
+    if torch.cuda.mem_get_info()[0] < 40e9:
+        pytest.skip("needs about 30 GB of free device memory")
     from paper_1112_5588_gb300 import build
     build.build()
     from paper_1112_5588_gb300 import pjds
@@ -70,26 +84,30 @@ def big():
     row_ptr = np.zeros(N + 1, np.int64)
     np.cumsum(_lengths(r_all), out=row_ptr[1:])
     nnz = int(row_ptr[-1])
-    col = np.empty(nnz, np.int32)
-    val = np.empty(nnz, np.float64)
-    step = 1 << 18
-    for s in range(0, N, step):
-        e = min(s + step, N)
-        c, v = _entries(r_all[s:e])
-        col[row_ptr[s]:row_ptr[e]] = c
-        val[row_ptr[s]:row_ptr[e]] = v
-    H = pjds.pjds_create(N, N, row_ptr, col, val, b=32, dtype="bf16")
-    assert H.n_stored + H.n_pad > 2**31
-    D = H.to_device("cuda")
-    H.destroy()
-    He = pjds.ellr_create(N, N, row_ptr, col, val, dtype="bf16")
-    assert He.n_stored > 2**31
-    E = He.to_device("cuda")
-    He.destroy()
-    del col, val
+    S = pjds.pjds_create_shape(N, N, row_ptr, b=32, dtype="bf16")
+    assert S.n_stored + S.n_pad > 2**31 and S.n_max == N_MAX
+    cs = S.col_start.copy()
+    perm = torch.from_numpy(S.perm.astype(np.int64)).cuda()
+    col = torch.empty(S.n_stored, dtype=torch.int32, device="cuda")
+    val = torch.empty(S.n_stored, dtype=torch.int16, device="cuda")
+    for j in range(S.n_max):
+        a, e = int(cs[j]), int(cs[j + 1])
+        col[a:e], val[a:e] = _diagonal(torch, perm[: e - a], j)
+    del perm
+    D = pjds.PjdsDevice(S, "cuda", col=col, val=val)
+    S.destroy()
+    # ELLPACK-R: entry j of row i at j * N + i
+    rows = torch.arange(N, dtype=torch.int64, device="cuda")
+    ecol = torch.empty(N * N_MAX, dtype=torch.int32, device="cuda")
+    eval_ = torch.empty(N * N_MAX, dtype=torch.int16, device="cuda")
+    for j in range(N_MAX):
+        ecol[j * N:(j + 1) * N], eval_[j * N:(j + 1) * N] = _diagonal(torch, rows, j)
+    E = _EllrView(pjds, torch, _lengths(rows).to(torch.int32), ecol, eval_, nnz)
+    del rows
     x = torch.from_numpy(_x()).cuda()
-    yield pjds, D, E, x, row_ptr
-    del D, E, x
+    torch.cuda.synchronize()
+    yield pjds, D, E, x
+    del D, E, x, col, val, ecol, eval_
     torch.cuda.empty_cache()
 
 
@@ -113,7 +131,7 @@ def _oracle_rows(oracle_lib, rows):
                                  dict(staged=1), dict(plan=1), "ellr"])
 def test_offsets_beyond_2_31_exact(big, oracle_lib, cfg):
     import torch
-    pjds, D, E, x, _ = big
+    pjds, D, E, x = big
     y = torch.full((N,), float("nan"), dtype=torch.float32, device="cuda")
     if cfg == "ellr":
         pjds.ellr_spmv(E, x, y)

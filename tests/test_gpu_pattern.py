@@ -99,3 +99,18 @@ def test_pattern_rejects_other_mappings(P, cfg):
     y = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
     with pytest.raises(P.PjdsError):
         P.pjds_spmv_pattern(D, x, y, **cfg)
+
+
+@pytest.mark.parametrize("k", [2, 8, 32])
+def test_pattern_spmm_bitwise_equals_oracle(P, oracle_lib, k):
+    import torch
+    from paper_1112_5588_gb300 import batch
+    A = synth.block_dense(n_brow=2_000, bs=4, nb=36, frac=0.05, seed=3)
+    D = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f64").to_device("cuda")
+    X = np.random.default_rng(k).uniform(-1, 1, (A.n_cols, k))
+    Y = torch.full((A.n_rows, k), float("nan"), dtype=torch.float64, device="cuda")
+    batch.spmm_pattern(D, torch.from_numpy(X).cuda(), Y)
+    torch.cuda.synchronize()
+    want = oracle_lib.crs_spmm(_ones(A), X)
+    got = Y.cpu().numpy()
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
