@@ -70,6 +70,13 @@ def test_spmv_and_ellr_write_only_y(mods, dtype, permute):
                 torch.cuda.synchronize()
                 assert intact(torch, raw, A.n_rows, D.vec_dtype), (cfg, b, A.n_rows)
                 assert torch.isfinite(y.float()).all(), cfg
+            # the pattern product (one thread per row, both tile orders)
+            for cfg in (dict(threads_per_row=1), dict(threads_per_row=1, tile_order=1)):
+                raw, y = guarded(torch, A.n_rows, D.vec_dtype)
+                pjds.pjds_spmv_pattern(D, x, y, **cfg)
+                torch.cuda.synchronize()
+                assert intact(torch, raw, A.n_rows, D.vec_dtype), ("pattern", cfg, b, A.n_rows)
+                assert torch.isfinite(y.float()).all(), cfg
         E = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype=dtype).to_device("cuda")
         raw, y = guarded(torch, A.n_rows, E.vec_dtype)
         pjds.ellr_spmv(E, torch.rand(A.n_cols, device="cuda", dtype=E.vec_dtype), y)
@@ -94,6 +101,10 @@ def test_permute_spmm_batch_write_only_their_outputs(mods):
         batch.spmm(Dk, X, flat.view(A.n_rows, k))
         torch.cuda.synchronize()
         assert intact(torch, raw, A.n_rows * k, Dk.vec_dtype), (dtype, k)
+        raw, flat = guarded(torch, A.n_rows * k, Dk.vec_dtype)
+        batch.spmm_pattern(Dk, X, flat.view(A.n_rows, k))
+        torch.cuda.synchronize()
+        assert intact(torch, raw, A.n_rows * k, Dk.vec_dtype), ("pattern", dtype, k)
     mats = [m() for m in MATS]
     devs = [pjds.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32).to_device("cuda") for M in mats]
     xs = [torch.rand(M.n_cols, device="cuda", dtype=torch.float64) for M in mats]
