@@ -504,6 +504,12 @@ def side_measurements(torch, pjds, A, x, D, xt, y, flush, args, dev, nbytes):
                              "alg_bytes": b_r, "speedup_vs_f64": round(t_p / tr, 3),
                              "kernel": kernel_name(pjds.pjds_spmv_resolve(Dr))}
         reduced[f"pjds_{dt}"] = (dt, yr.cpu().numpy().copy())
+        # its gather ceiling: the same launch without the value stream
+        yp = torch.empty_like(yr)
+        tpat = med(time_launches(torch, lambda: pjds.pjds_spmv_pattern(Dr, xr, yp), K, W, flush))
+        out[f"pjds_{dt}"]["gather_ceiling_us"] = round(tpat * 1e6, 2)
+        out[f"pjds_{dt}"]["frac_of_min_hbm_gather_ceiling"] = round(
+            (b_r / tr) / min(peak * 1e9, b_r / tpat), 4)
         del Dr, xr, yr
     # ELLPACK-R with fp32 values on the same matrix (Table 1's single-precision row)
     E32 = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype="f32")

@@ -287,10 +287,11 @@ int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *ou
  * and the y stores of the product and nothing else. Its time is therefore a
  * floor for the product's time with the same traversal, the gather ceiling
  * against which the product is measured besides HBM bandwidth (Eq. 1: the
- * alpha term, the traffic the right-hand side costs, is this part). One
- * thread per row only: a configuration that resolves to the per-tile plan,
- * the staged kernel, several rows or several threads per row returns
- * PJDS_EINVAL. The paper has no counterpart of this call.
+ * alpha term, the traffic the right-hand side costs, is this part). The
+ * uniform mappings with one thread per row (one, two or four rows per
+ * thread) only: a configuration that resolves to the per-tile plan, the
+ * staged kernel or several threads per row returns PJDS_EINVAL. The paper
+ * has no counterpart of this call.
  */
 int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
 

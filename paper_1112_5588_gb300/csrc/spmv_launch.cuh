@@ -67,14 +67,19 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
 #define PJDS_ARGS val, A->col, A->col_start, A->block_len, A->perm, order, x, y, A->n_rows, A->n_pad, A->b
   const int U = c.unroll;
 #define PJDS_ROWS(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
-#define PJDS_PAT(UU) dev::pjds_rows_kernel<TV, TX, IDX, 1, UU, SC, true><<<g, blk, 0, s>>>(PJDS_ARGS)
+#define PJDS_PAT(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC, true><<<g, blk, 0, s>>>(PJDS_ARGS)
 #define PJDS_TPR(TT, UU) dev::pjds_tpr_kernel<TV, TX, IDX, TT, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
   if (c.pattern) {
-    if (T != 1 || R != 1) return set_error(PJDS_EINVAL, "the pattern product runs one thread per row");
-    if (U == 4) PJDS_PAT(4);
-    else if (U == 8) PJDS_PAT(8);
-    else if (U == 16) PJDS_PAT(16);
-    else return set_error(PJDS_EINVAL, "unroll must be 4, 8 or 16 for one row per thread");
+    if (T != 1) return set_error(PJDS_EINVAL, "the pattern product runs one thread per row");
+    if (R == 1 && U == 4) PJDS_PAT(1, 4);
+    else if (R == 1 && U == 8) PJDS_PAT(1, 8);
+    else if (R == 1 && U == 16) PJDS_PAT(1, 16);
+    else if (R == 2 && U == 2) PJDS_PAT(2, 2);
+    else if (R == 2 && U == 4) PJDS_PAT(2, 4);
+    else if (R == 2 && U == 8) PJDS_PAT(2, 8);
+    else if (R == 4 && U == 2) PJDS_PAT(4, 2);
+    else if (R == 4 && U == 4) PJDS_PAT(4, 4);
+    else return set_error(PJDS_EINVAL, "unroll %d is not available for %d rows per thread", U, R);
   } else if (T == 1 && R == 1) {
     if (U == 4) PJDS_ROWS(1, 4);
     else if (U == 8) PJDS_ROWS(1, 8);

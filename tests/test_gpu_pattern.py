@@ -42,7 +42,8 @@ SHAPES = [
 # otherwise default to several threads per row
 CFGS = [dict(threads_per_row=1), dict(threads_per_row=1, tile_order=-1), dict(threads_per_row=1, tile_order=1),
         dict(threads_per_row=1, unroll=8), dict(threads_per_row=1, unroll=16, block_threads=128),
-        dict(threads_per_row=1, index64=1)]
+        dict(threads_per_row=1, index64=1), dict(rows_per_thread=2), dict(rows_per_thread=4, tile_order=1),
+        dict(rows_per_thread=2, unroll=8, index64=1)]
 
 
 @pytest.mark.parametrize("cfg", CFGS, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
@@ -90,7 +91,7 @@ def test_pattern_permuted_basis(P, oracle_lib):
     assert np.array_equal(y.cpu().numpy().view(np.uint64), want.view(np.uint64))
 
 
-@pytest.mark.parametrize("cfg", [dict(plan=1), dict(threads_per_row=2), dict(rows_per_thread=2), dict(staged=1)])
+@pytest.mark.parametrize("cfg", [dict(plan=1), dict(threads_per_row=2), dict(staged=1)])
 def test_pattern_rejects_other_mappings(P, cfg):
     import torch
     A = synth.zipf_rows(70_000, s=2.0, len_max=512, seed=8)
