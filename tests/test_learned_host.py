@@ -90,3 +90,26 @@ def test_committed_model_and_data_are_consistent(L):
     # the model's feature range is the training matrices' range
     F = data["features"][:2000]
     assert np.allclose(np.array(m.feat_lo), F.min(0)) and np.allclose(np.array(m.feat_hi), F.max(0))
+
+
+def test_pick_needs_the_sweep_outside_the_range(L):
+    # the range check runs on the host: outside the model's range, or without
+    # a model, pjds_tune_pick needs the sweep's arena and says so (no GPU work)
+    import ctypes
+    from paper_1112_5588_gb300 import pjds, tune
+    A = synth.hmep_like(n=20_000, seed=5)
+    rp, col, val = pjds._crs_args(A.row_ptr, A.col, A.val)
+    cands = tune.default_space(("f64",))
+    m = L.init(1)
+    L.fit_range(m, np.zeros((4, 8), np.float32))  # a range no matrix of 20k rows lies in
+    for model in (ctypes.byref(m), None):
+        out = L.Pick()
+        rc = L._lib.pjds_tune_pick(A.n_rows, A.n_cols, rp.ctypes.data, col.ctypes.data, val.ctypes.data, model,
+                                   tune._to_cands(cands), len(cands), 3, None, 0, None, 0, None, 0,
+                                   ctypes.byref(out), None)
+        assert rc == -1 and "sweep arena" in pjds.lib().pjds_last_error().decode()
+    assert out.n_outside == 0  # no model: nothing compared
+    out = L.Pick()
+    L._lib.pjds_tune_pick(A.n_rows, A.n_cols, rp.ctypes.data, col.ctypes.data, val.ctypes.data, ctypes.byref(m),
+                          tune._to_cands(cands), len(cands), 3, None, 0, None, 0, None, 0, ctypes.byref(out), None)
+    assert out.n_outside >= 3  # N, nnz and the mean row length at least
