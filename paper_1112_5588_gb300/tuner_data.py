@@ -64,10 +64,11 @@ def make_matrix(p: dict):
 
 
 def generate(n_train: int, n_test: int, seed: int = 2024, n_lo: float = 1e4, n_hi: float = 2e7, reps: int = 3,
-             log=sys.stderr, checkpoint: str | None = None) -> dict:
+             log=sys.stderr, checkpoint: str | None = None, resume: dict | None = None) -> dict:
     """Time the candidate space (tune.default_space: 36 candidates per
     precision) on n_train + n_test synthetic matrices; with `checkpoint`, the
-    data gathered so far is saved there every 100 matrices."""
+    data gathered so far is saved there every 100 matrices; `resume` (such a
+    checkpoint, same arguments) continues after its last matrix."""
     from . import learned, tune
     cands = tune.default_space(DTYPES)
     n_all = n_train + n_test
@@ -75,12 +76,18 @@ def generate(n_train: int, n_test: int, seed: int = 2024, n_lo: float = 1e4, n_h
     times = np.full((n_all, len(cands)), np.nan, np.float64)
     sizes = np.zeros((n_all, 3), np.int64)  # n_rows, nnz, longest row
     params = []
+    if resume is not None:
+        if json.loads(str(resume["cands"])) != cands:
+            raise ValueError("the checkpoint was taken over another candidate space")
+        params = json.loads(str(resume["params"]))
+        k0 = len(params)
+        feats[:k0], times[:k0], sizes[:k0] = resume["features"], resume["times_us"], resume["sizes"]
     t0 = time.time()
 
     def pack(k):
         return {"features": feats[:k], "times_us": times[:k], "sizes": sizes[:k], "n_train": min(n_train, k),
                 "cands": json.dumps(cands), "params": json.dumps(params[:k])}
-    for i in range(n_all):
+    for i in range(len(params), n_all):
         p = matrix_params(i, seed if i < n_train else seed + 1, n_lo, n_hi)
         A = make_matrix(p)
         feats[i] = learned.features(A)
@@ -301,6 +308,7 @@ def main(argv=None) -> int:
     g.add_argument("--n-hi", type=float, default=2e7)
     g.add_argument("--out", required=True)
     g.add_argument("--checkpoint", default=None)
+    g.add_argument("--resume", default=None, help="a checkpoint of the same command to continue from")
     t = sub.add_parser("train")
     t.add_argument("data")
     t.add_argument("--model", required=True)
@@ -323,7 +331,8 @@ def main(argv=None) -> int:
     pf.add_argument("test")
     a = ap.parse_args(argv)
     if a.cmd == "generate":
-        d = generate(a.n_train, a.n_test, a.seed, a.n_lo, a.n_hi, checkpoint=a.checkpoint)
+        d = generate(a.n_train, a.n_test, a.seed, a.n_lo, a.n_hi, checkpoint=a.checkpoint,
+                     resume=dict(np.load(a.resume, allow_pickle=False)) if a.resume else None)
         np.savez_compressed(a.out, **d)
         print(json.dumps({"saved": a.out, "matrices": a.n_train + a.n_test}))
     elif a.cmd == "train":
