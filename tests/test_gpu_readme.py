@@ -23,4 +23,5 @@ def test_readme_examples_run():
     # the first example's product is finite and the batch wrote its outputs
     assert torch.isfinite(ns["y"]).all()
     assert all(torch.isfinite(t).all() for t in ns["ys"])
-    assert ns["cand"]["threads_per_row"] in (1, 2, 4, 8)
+    assert ns["choice"]["source"] in ("model", "sweep") and ns["choice"]["b"] in (32, 64, 128, 256)
+    assert torch.isfinite(ns["y_ceiling"]).all()
