@@ -344,17 +344,20 @@ PLAN_SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("name,make", PLAN_SHAPES, ids=[s[0] for s in PLAN_SHAPES])
+# the permuted basis needs a square matrix: the rectangular shape runs in the original basis only
+PLAN_CASES = [(name, make, permute) for name, make in PLAN_SHAPES for permute in (False, True)
+              if not (permute and name == "ragged_long")]
+
+
+@pytest.mark.parametrize("name,make,permute", PLAN_CASES, ids=[f"{c[0]}-{'perm' if c[2] else 'orig'}" for c in PLAN_CASES])
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("permute", [False, True])
 @pytest.mark.parametrize("b", [32, 128])
-def test_plan_rows_bit_identical_to_uniform_mappings(P, name, make, dtype, permute, b):
+def test_plan_rows_bit_identical_to_uniform_mappings(P, name, make, permute, dtype, b):
     # each row of the per-tile mapping is summed as the uniform mapping with
     # its tile's lanes per row sums it (one thread per row for kinds 0, 1, 3)
     torch = _torch()
     A = make()
-    if permute and A.n_rows != A.n_cols:
-        pytest.skip("permuted basis needs a square matrix")
+    assert not permute or A.n_rows == A.n_cols
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=b, dtype=dtype, permute_cols=permute)
     D = H.to_device("cuda")
     xt = torch.from_numpy(synth.vector(A.n_cols, seed=24)).to(device="cuda", dtype=D.vec_dtype)
