@@ -55,11 +55,8 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
   const bool u_ok = T > 1 ? (U == 2 || U == 4)
                           : R == 1 ? (U == 4 || U == 8 || U == 16) : R == 2 ? (U == 2 || U == 4 || U == 8) : (U == 2 || U == 4);
   if (!u_ok) return set_error(PJDS_EINVAL, "unroll %d is not available for rows_per_thread %d, threads_per_row %d", U, R, T);
-  const bool wide = c.block_threads == 1024 && R == 1 && T == 1 && !c.staged && !c.plan && !c.pattern &&
-                    (c.unroll == 4 || c.unroll == 8);
-  if (!wide && (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32))
-    return set_error(PJDS_EINVAL,
-                     "block_threads must be a multiple of 32 in [32, 512] (or 1024 with one row per thread, unroll 4 or 8)");
+  if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32)
+    return set_error(PJDS_EINVAL, "block_threads must be a multiple of 32 in [32, 512]");
   if (R > 1) {
     const uintptr_t va = (uintptr_t)A->val, ca = (uintptr_t)A->col;
     const int vb = value_bytes(A->dtype) * R, need_v = vb < 16 ? vb : 16, need_c = 4 * R < 16 ? 4 * R : 16;
@@ -202,7 +199,6 @@ extern "C" int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, cons
   if (rc) return rc;
   if (c.plan || c.staged || c.threads_per_row != 1)
     return set_error(PJDS_EINVAL, "the pattern product runs the uniform mappings with one thread per row only");
-  if (c.block_threads > 512) return set_error(PJDS_EINVAL, "the pattern product runs CTAs of at most 512 threads");
   c.pattern = 1;
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
 }

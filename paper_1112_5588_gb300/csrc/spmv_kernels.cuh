@@ -221,8 +221,8 @@ __device__ __forceinline__ TX gather_n(const TX *__restrict__ x, int32_t c, int3
 // on j < L, so a short row issues all of its loads in ceil(L/U) rounds.
 // PAT: the pattern product (every stored value taken as 1, val not read):
 // the same column stream, x gathers and y stores, plain additions.
-template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER, bool PAT = false, int MAXT = 512>
-__global__ void __launch_bounds__(MAXT) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
+template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER, bool PAT = false>
+__global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
                                                         const int64_t *__restrict__ col_start,
                                                         const int32_t *__restrict__ block_len,
                                                         const int32_t *__restrict__ perm,

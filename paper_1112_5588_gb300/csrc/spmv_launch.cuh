@@ -80,11 +80,6 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
     else if (R == 4 && U == 2) PJDS_PAT(4, 2);
     else if (R == 4 && U == 4) PJDS_PAT(4, 4);
     else return set_error(PJDS_EINVAL, "unroll %d is not available for %d rows per thread", U, R);
-  } else if (T == 1 && R == 1 && nt == 1024) {
-    // 1024-thread CTAs: 32 consecutive tiles of the traversal order per CTA
-    if (U == 4) dev::pjds_rows_kernel<TV, TX, IDX, 1, 4, SC, false, 1024><<<g, blk, 0, s>>>(PJDS_ARGS);
-    else if (U == 8) dev::pjds_rows_kernel<TV, TX, IDX, 1, 8, SC, false, 1024><<<g, blk, 0, s>>>(PJDS_ARGS);
-    else return set_error(PJDS_EINVAL, "unroll must be 4 or 8 with 1024-thread CTAs");
   } else if (T == 1 && R == 1) {
     if (U == 4) PJDS_ROWS(1, 4);
     else if (U == 8) PJDS_ROWS(1, 8);
