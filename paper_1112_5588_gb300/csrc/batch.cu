@@ -48,8 +48,11 @@ struct V16<double> {
 // per row). Wider lanes spread the loads of col_start, col and val and the
 // address arithmetic over more fused multiply-adds. Row offsets into X and Y
 // are 32-bit indices widened in the multiply (one wide multiply-add each).
-// PAT: the pattern product Y = S X (every stored value taken as 1, val not
-// read): the same column stream, X-row gathers and Y stores, plain additions.
+// PAT: the pattern product Y = S X (every stored value taken as 1, the
+// matrix's values not read): val is the address of eight ones
+// (dev::pattern_ones_address), read where the product reads its values, so
+// the kernel keeps the product's instructions, registers and occupancy and
+// only the value stream is missing; fma(1, x, acc) is acc + x rounded once.
 template <typename TV, typename TX, typename IDX, bool SCATTER, int CH, bool PAT = false>
 __global__ void __launch_bounds__(BT)
     spmm_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ col_start,
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(BT)
         }
 #endif
         c[u] = __ldcs(col + o);
-        if constexpr (!PAT) v[u] = dev::ld_stream1(val + o);
+        v[u] = dev::ld_stream1(PAT ? val + dev::pattern_slot(val + o) : val + o);  // PAT: val holds the ones
       } else {
         c[u] = -1;
         v[u] = TV{};
@@ -102,12 +105,8 @@ __global__ void __launch_bounds__(BT)
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        if constexpr (PAT)
-          acc[w] = c[u] >= 0 ? acc[w] + (TA)xv[u][w] : acc[w];
-        else
-          acc[w] = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u][w], acc[w]) : acc[w];
-      }
+      for (int w = 0; w < W; ++w)
+        acc[w] = c[u] >= 0 ? dev::fma_acc(dev::to_acc(v[u]), (TA)xv[u][w], acc[w]) : acc[w];
   }
   TX out[W];
 #pragma unroll
@@ -216,6 +215,12 @@ static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cud
   if (grid <= 0) return PJDS_OK;
   if (grid > 0x7fffffffLL) return set_error(PJDS_EOVERFLOW, "grid too large");
   const TV *val = static_cast<const TV *>(A->val);
+  if constexpr (PAT) {
+    const void *ones = nullptr;
+    const cudaError_t e = dev::pattern_ones_address<TV>(&ones);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "pattern values: %s", cudaGetErrorString(e));
+    val = static_cast<const TV *>(ones);
+  }
   const TX *x = static_cast<const TX *>(X);
   TX *y = static_cast<TX *>(Y);
   const bool small = A->n_stored + A->n_pad < 0x7fffffffLL, sc = !A->permute_cols;

@@ -136,6 +136,41 @@ __device__ __forceinline__ bf16_t ld_stream1(const bf16_t *p) {
   return v;
 }
 
+// Values of the pattern products (every stored value taken as 1): the
+// launcher passes the device address of these 8 ones as the kernel's val,
+// and the pattern kernels read val + pattern_slot(val + o) (always a one)
+// where the product reads val + o. They issue the product's instructions
+// with its registers and occupancy, while the value stream stays in L1, and
+// fma(1, x, acc) rounds acc + x once: the pattern product's sum exactly.
+static __device__ __align__(16) double g_ones_f64[8] = {1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
+static __device__ __align__(16) float g_ones_f32[8] = {1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f};
+static __device__ __align__(16) bf16_t g_ones_bf16[8] = {{0x3F80}, {0x3F80}, {0x3F80}, {0x3F80},
+                                                         {0x3F80}, {0x3F80}, {0x3F80}, {0x3F80}};
+
+// The product's value address, kept live (the compiler may not fold it
+// away), reduced to a slot of the ones: 0 for every address the product
+// reads (values are aligned to their size).
+template <typename TV>
+__device__ __forceinline__ int pattern_slot(const TV *p) {
+  asm volatile("" : "+l"(p));
+  return (int)(reinterpret_cast<uintptr_t>(p) & 3);
+}
+
+// Device address of this translation unit's ones of type TV (host code).
+template <typename TV>
+inline cudaError_t pattern_ones_address(const void **out) {
+  void *p = nullptr;
+  cudaError_t e;
+  if constexpr (sizeof(TV) == 8)
+    e = cudaGetSymbolAddress(&p, g_ones_f64);
+  else if constexpr (sizeof(TV) == 4)
+    e = cudaGetSymbolAddress(&p, g_ones_f32);
+  else
+    e = cudaGetSymbolAddress(&p, g_ones_bf16);
+  *out = p;
+  return e;
+}
+
 // Tile traversal order: logical row r is row r mod 32 of tile order[r / 32]
 // (tiles of 32 sorted rows). Rewrites r in place; false for an entry outside
 // the table's range (the thread then has no row).
@@ -220,7 +255,8 @@ __device__ __forceinline__ TX gather_n(const TX *__restrict__ x, int32_t c, int3
 // j-loop runs in chunks of U jagged diagonals; a chunk's loads are predicated
 // on j < L, so a short row issues all of its loads in ceil(L/U) rounds.
 // PAT: the pattern product (every stored value taken as 1, val not read):
-// the same column stream, x gathers and y stores, plain additions.
+// the same column stream, x gathers, fused multiply-adds (by the ones of
+// pattern_ones, L1 hits) and y stores.
 template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER, bool PAT = false>
 __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
                                                         const int64_t *__restrict__ col_start,
@@ -252,7 +288,10 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
       }
       if (live) {
         ld_stream<R>(col + o, c[u]);
-        if constexpr (!PAT) ld_stream<R>(val + o, v[u]);
+        if constexpr (PAT)
+          ld_stream<R>(val + pattern_slot(val + o), v[u]);  // val: the ones
+        else
+          ld_stream<R>(val + o, v[u]);
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -269,12 +308,7 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if constexpr (PAT)
-          acc[r] = c[u][r] >= 0 ? acc[r] + (TA)xv[u][r] : acc[r];
-        else
-          acc[r] = c[u][r] >= 0 ? fma_acc(to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
-      }
+      for (int r = 0; r < R; ++r) acc[r] = c[u][r] >= 0 ? fma_acc(to_acc(v[u][r]), (TA)xv[u][r], acc[r]) : acc[r];
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {

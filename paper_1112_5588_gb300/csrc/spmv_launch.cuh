@@ -54,6 +54,12 @@ template <typename TV, typename TX, typename IDX, bool SC>
 int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaStream_t s) {
   if (c.staged) return launch_staged<TV, TX, IDX, SC>(A, x, y, s);
   const TV *val = static_cast<const TV *>(A->val);
+  if (c.pattern) {  // the pattern kernels read their values from eight ones
+    const void *ones = nullptr;
+    const cudaError_t e = dev::pattern_ones_address<TV>(&ones);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "pattern values: %s", cudaGetErrorString(e));
+    val = static_cast<const TV *>(ones);
+  }
   const int R = c.rows_per_thread, T = c.threads_per_row, nt = c.block_threads;
   const int64_t work = T > 1 ? (int64_t)A->n_pad * T : ((int64_t)A->n_pad + R - 1) / R;
   const int64_t grid = (work + nt - 1) / nt;
