@@ -35,7 +35,7 @@
  *   oracle_round_f32/bf16  the value a reduced-precision store holds
  *                          (Table 1 compares single and double precision).
  *
- * Readings where the paper is silent (each is also listed in the design notes):
+ * Readings where the paper is silent:
  *   - equal-length rows keep their original order (stable sort);
  *   - pad entries hold value +0.0 and column index -1 and are never used;
  *   - rows are padded up to a multiple of b with empty rows;

@@ -57,7 +57,7 @@ def test_static_workspace_matches_caller_workspace_twice(mods, oracle_lib, lo):
         assert rc == 0, pjds.lib().pjds_last_error()
         torch.cuda.synchronize()
         # nothing was allocated on the device by the second call (the first
-        # may still load the module that holds the array, where the driver
+        # may still load the module that holds the array, where the CUDA driver
         # loads modules lazily)
         if call == 1:
             assert torch.cuda.mem_get_info()[0] == free_before
