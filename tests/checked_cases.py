@@ -3,8 +3,9 @@ with PJDS_LIBRARY=checked, which loads libpjds_checked.so).
 
 Clean: every mapping of the product with device-side extent checks (one and
 T threads per row, several rows per thread, tile order, per-tile mapping,
-64-bit offsets), ELLPACK-R and the batched launch, on ragged, spread and
-banded matrices, must leave the check word at 0 and (fp64) match the oracle.
+64-bit offsets), the pattern product, ELLPACK-R and the batched launch, on
+ragged, spread and banded matrices, must leave the check word at 0 and
+(fp64) match the oracle.
 
 Planted: an index put out of range in a device copy of a matrix (a column
 beyond n_cols, a perm entry beyond n_rows, a jagged-diagonal offset beyond
@@ -76,6 +77,13 @@ def main():
                     if dt == "f64":
                         ok = ok and parity.check_fp64(y.cpu().numpy(), yref, absax, lens)["ok"]
                     res["clean"].append([name, dt, b, cfg, w, ok])
+                # the pattern product (the gather ceiling) with one and two rows per thread
+                for cfg in (dict(threads_per_row=1), dict(rows_per_thread=2)):
+                    y = torch.full((D.n_rows,), float("nan"), dtype=D.vec_dtype, device="cuda")
+                    pjds.pjds_spmv_pattern(D, xt, y, **cfg)
+                    torch.cuda.synchronize()
+                    w = pjds.pjds_check_word(clear=True)
+                    res["clean"].append([name, dt, b, dict(pattern=1, **cfg), w, bool(torch.isfinite(y).all())])
             E = pjds.ellr_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, dtype=dt).to_device("cuda")
             y = torch.full((A.n_rows,), float("nan"), dtype=E.vec_dtype, device="cuda")
             pjds.ellr_spmv(E, torch.from_numpy(x).to("cuda", E.vec_dtype), y)
