@@ -779,6 +779,8 @@ def batching_leg(torch, pjds, args, dev, flush):
         nbytes += alg_bytes(M.n_rows, M.n_cols, M.nnz, 8, 8)
     B = batch.Batch(devs, xs, ys)
     t_batch = statistics.median(time_launches(torch, lambda: B.run(use_graph=True), 10, 3, flush))
+    t_batch_pat = statistics.median(time_launches(torch, B.run_pattern, 10, 3, flush))
+    t_batch_direct = statistics.median(time_launches(torch, lambda: B.run(use_graph=False), 10, 3, flush))
 
     def separate():
         for Dm, xm, ym in zip(devs, xs, ys):
@@ -797,6 +799,10 @@ def batching_leg(torch, pjds, args, dev, flush):
     out["multi_matrix"] = {"n_mats": 64, "total_rows": int(sizes.sum()), "nnz": int(nnz), **B.info(),
                            "persistent_graph_us": round(t_batch * 1e6, 2),
                            "persistent_graph_gbs": round(nbytes / t_batch / 1e9, 1),
+                           "frac_of_hbm": round(nbytes / t_batch / 1e9 / hbm_peak()[0], 4),
+                           "persistent_direct_us": round(t_batch_direct * 1e6, 2),
+                           "gather_ceiling_us": round(t_batch_pat * 1e6, 2),
+                           "frac_of_gather_ceiling": round(t_batch_pat / t_batch_direct, 4),
                            "separate_launches_us": round(t_sep * 1e6, 2),
                            "separate_launches_graph_us": round(t_sep_graph * 1e6, 2),
                            "speedup_vs_separate": round(t_sep / t_batch, 3),
@@ -878,6 +884,8 @@ def spread_leg(torch, pjds, args, dev, flush):
         nb = alg_bytes(A.n_rows, A.n_cols, A.nnz, vb, xb)
         t_def = med(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 20, 3, flush))
         t_hot = med(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 20, 3, None))
+        yp = torch.empty_like(y)
+        t_pat = med(time_launches(torch, lambda: pjds.pjds_spmv_pattern(D, x, yp), 20, 3, flush))
         uni = {t: med(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, x, y, threads_per_row=t, plan=-1), 20, 3, flush))
                for t in (1, 2, 4, 8)}
         best = min(uni, key=uni.get)
@@ -885,6 +893,7 @@ def spread_leg(torch, pjds, args, dev, flush):
                    "default_us": round(t_def * 1e6, 2), "default_gbs": round(nb / t_def / 1e9, 1),
                    "working_set_mb": round(nb / 1e6, 1), "l2_mb": 129,
                    "default_l2_warm_us": round(t_hot * 1e6, 2),
+                   "gather_ceiling_us": round(t_pat * 1e6, 2), "frac_of_gather_ceiling": round(t_pat / t_def, 4),
                    "bound": ("L2-resident working set: measured cold (L2 flushed before each launch) and warm; "
                              "a warm time near the cold one means latency, not DRAM, sets it"),
                    "uniform_us": {f"T{t}": round(v * 1e6, 2) for t, v in uni.items()},

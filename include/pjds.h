@@ -281,17 +281,17 @@ int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds_launch *ou
 /*
  * Pattern product y = S x, S the sparsity pattern of A (every stored entry
  * taken as 1): sorted row i sums x[col[col_start[j] + i]] for j < len(i), in
- * order, with plain additions, and writes y[perm[i]] (y[i] in the permuted
- * basis). It runs the traversal pjds_spmv_cfg would run for cfg (NULL: the
+ * the order of the product with the same mapping, and writes y[perm[i]]
+ * (y[i] in the permuted basis). It runs the traversal pjds_spmv_cfg would run for cfg (NULL: the
  * pjds_spmv default) without reading val: the column stream, the x gathers
  * and the y stores of the product and nothing else. Its time is therefore a
  * floor for the product's time with the same traversal, the gather ceiling
  * against which the product is measured besides HBM bandwidth (Eq. 1: the
- * alpha term, the traffic the right-hand side costs, is this part). The
- * uniform mappings with one thread per row (one, two or four rows per
- * thread) only: a configuration that resolves to the per-tile plan, the
- * staged kernel or several threads per row returns PJDS_EINVAL. The paper
- * has no counterpart of this call.
+ * alpha term, the traffic the right-hand side costs, is this part). Every
+ * mapping but the staged kernel (PJDS_EINVAL): the kernel is the product's
+ * own, with the values read from eight ones in L1 instead of val, so it keeps
+ * the product's instructions, registers and occupancy; fma(1, x, acc) is
+ * acc + x rounded once. The paper has no counterpart of this call.
  */
 int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);
 

@@ -128,6 +128,17 @@ int pjds_batch_tune_rule(int32_t n_mats, const pjds_dev *mats, const void *const
  */
 int pjds_batch_run(pjds_batch *h, int32_t use_graph, void *stream);
 
+/*
+ * The pattern products of the batch in one launch of the same plan (no graph):
+ * y_m = S_m x_m, S_m the sparsity pattern of matrix m (every stored entry taken
+ * as 1), with the batched kernel's instructions, registers and occupancy, its
+ * values read from eight ones in L1 instead of each matrix's values. Its time
+ * is a floor for pjds_batch_run's: the gathers, column streams and stores of
+ * the whole batch, the gather ceiling it is measured against. Writes the same
+ * ys as pjds_batch_run. The paper has no counterpart of this call.
+ */
+int pjds_batch_run_pattern(pjds_batch *h, void *stream);
+
 /* Number of tiles and CTAs of the plan (for reporting). */
 int pjds_batch_info(const pjds_batch *h, int32_t *n_tiles, int32_t *n_ctas);
 

@@ -23,6 +23,7 @@ for _name, _res, _args in (
         ("pjds_batch_tune_rule", ctypes.c_int, [_i32, _P(_p._PjdsDevS), _P(_vp), _P(_vp), _P(_i32), _i32, _i32, _vp,
                                                 _sz, _vp, _sz, _P(ctypes.c_double), _P(_i32), _vp]),
         ("pjds_batch_run", ctypes.c_int, [_vp, _i32, _vp]),
+        ("pjds_batch_run_pattern", ctypes.c_int, [_vp, _vp]),
         ("pjds_batch_info", ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
         ("pjds_batch_destroy", ctypes.c_int, [_vp])):
     getattr(_lib, _name).restype = _res
@@ -95,6 +96,11 @@ class Batch:
 
     def run(self, use_graph: bool = True, stream=None):
         _p._check(_lib.pjds_batch_run(self._h, 1 if use_graph else 0, _p._stream_ptr(stream)), "pjds_batch_run")
+
+    def run_pattern(self, stream=None):
+        """The pattern products of the batch (pjds_batch_run_pattern): the
+        same launch without the value streams, its gather ceiling."""
+        _p._check(_lib.pjds_batch_run_pattern(self._h, _p._stream_ptr(stream)), "pjds_batch_run_pattern")
 
     def info(self) -> dict:
         nt, nc = _i32(), _i32()

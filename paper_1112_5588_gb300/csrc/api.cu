@@ -197,8 +197,7 @@ extern "C" int pjds_spmv_pattern(const pjds_dev *A, const void *x, void *y, cons
   LaunchCfg c;
   rc = resolve_cfg(A, cfg, c);
   if (rc) return rc;
-  if (c.plan || c.staged || c.threads_per_row != 1)
-    return set_error(PJDS_EINVAL, "the pattern product runs the uniform mappings with one thread per row only");
+  if (c.staged) return set_error(PJDS_EINVAL, "the pattern product does not run the staged kernel");
   c.pattern = 1;
   return dispatch_pjds(A, x, y, c, static_cast<cudaStream_t>(stream));
 }

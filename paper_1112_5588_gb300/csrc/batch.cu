@@ -127,10 +127,12 @@ using namespace pjds::tiles;
 // counter until none is left: tiles of one lane per row have one row per
 // thread, tiles of 2, 4 or 8 lanes per row BT / lanes rows. No CTA ever waits
 // for another.
-template <typename TV, typename TX>
+// PAT: the pattern products of every matrix (ones: the address of eight
+// ones, read in place of each matrix's values; see run_tile).
+template <typename TV, typename TX, bool PAT = false>
 __device__ __forceinline__ void
     batch_body(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
-                 int32_t *__restrict__ counter) {
+                 int32_t *__restrict__ counter, const void *ones) {
   __shared__ int32_t s_tile;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
@@ -139,26 +141,28 @@ __device__ __forceinline__ void
     __syncthreads();
     if (t >= n_tiles) return;
     const int4 tl = tiles[t];
-    const Desc d = descs[tl.x];
-    run_tile<TV, TX>(d, tl);
+    Desc d = descs[tl.x];
+    if constexpr (PAT) d.val = ones;
+    run_tile<TV, TX, PAT>(d, tl);
   }
 }
 
-template <typename TV, typename TX>
+template <typename TV, typename TX, bool PAT = false>
 __global__ void __launch_bounds__(BT)
     batch_kernel(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
-                 int32_t *__restrict__ counter) {
-  batch_body<TV, TX>(descs, tiles, n_tiles, counter);
+                 int32_t *__restrict__ counter, const void *ones) {
+  batch_body<TV, TX, PAT>(descs, tiles, n_tiles, counter, ones);
 }
 
 // fp64 values: six resident CTAs per SM. Without the bound the four-row path
 // takes the kernel from 40 to 48 registers and five CTAs per SM (253 against
 // 237 us on the Zipf batch); fp32 and bf16 stay at 40 registers unbounded,
 // while the same bound made fp32 spill (222 against 214 us).
+template <bool PAT = false>
 __global__ void __launch_bounds__(BT, 6)
     batch_kernel_f64(const Desc *__restrict__ descs, const int4 *__restrict__ tiles, int32_t n_tiles,
-                     int32_t *__restrict__ counter) {
-  batch_body<double, double>(descs, tiles, n_tiles, counter);
+                     int32_t *__restrict__ counter, const void *ones) {
+  batch_body<double, double, PAT>(descs, tiles, n_tiles, counter, ones);
 }
 
 static inline size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -403,7 +407,7 @@ static int batch_plan(int32_t n_mats, const pjds_dev *mats, const void *const *x
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (dt == PJDS_F64)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_f64, BT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_f64<false>, BT, 0);
   else if (dt == PJDS_F32)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float, float>, BT, 0);
   else
@@ -449,15 +453,24 @@ extern "C" int pjds_batch_create_rule(int32_t n_mats, const pjds_dev *mats, cons
   return batch_plan(n_mats, mats, xs, ys, nullptr, min_len, plan_dev, plan_bytes, out, stream);
 }
 
+template <bool PAT = false>
 static int batch_issue(pjds_batch *h, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(h->counter, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return set_error(PJDS_ECUDA, "reset counter: %s", cudaGetErrorString(e));
+  const void *ones = nullptr;
+  if constexpr (PAT) {
+    e = h->dtype == PJDS_F64   ? dev::pattern_ones_address<double>(&ones)
+        : h->dtype == PJDS_F32 ? dev::pattern_ones_address<float>(&ones)
+                               : dev::pattern_ones_address<dev::bf16_t>(&ones);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "pattern values: %s", cudaGetErrorString(e));
+  }
   if (h->dtype == PJDS_F64)
-    batch_kernel_f64<<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
+    batch_kernel_f64<PAT><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter, ones);
   else if (h->dtype == PJDS_F32)
-    batch_kernel<float, float><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
+    batch_kernel<float, float, PAT><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter, ones);
   else
-    batch_kernel<dev::bf16_t, float><<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter);
+    batch_kernel<dev::bf16_t, float, PAT>
+        <<<h->n_ctas, BT, 0, s>>>(h->descs, h->tiles, h->n_tiles, h->counter, ones);
   e = cudaGetLastError();
   return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "batch launch: %s", cudaGetErrorString(e));
 }
@@ -490,6 +503,13 @@ extern "C" int pjds_batch_run(pjds_batch *h, int32_t use_graph, void *stream) {
   }
   cudaError_t e = cudaGraphLaunch(h->exec, s);
   return e == cudaSuccess ? PJDS_OK : set_error(PJDS_ECUDA, "batch graph launch: %s", cudaGetErrorString(e));
+}
+
+extern "C" int pjds_batch_run_pattern(pjds_batch *h, void *stream) {
+  clear_error();
+  if (!h) return set_error(PJDS_EINVAL, "h is NULL");
+  if (h->n_tiles == 0) return PJDS_OK;
+  return batch_issue<true>(h, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int pjds_batch_info(const pjds_batch *h, int32_t *n_tiles, int32_t *n_ctas) {

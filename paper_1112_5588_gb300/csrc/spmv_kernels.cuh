@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
 
 // T consecutive lanes share one sorted row: lane s takes jagged diagonals
 // j = s, s+T, ...; the T partial sums are added with shuffles (fixed tree).
-template <typename TV, typename TX, typename IDX, int T, int U, bool SCATTER>
+template <typename TV, typename TX, typename IDX, int T, int U, bool SCATTER, bool PAT = false>
 __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
                                                         const int64_t *__restrict__ col_start,
                                                         const int32_t *__restrict__ block_len,
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(512) pjds_tpr_kernel(const TV *__restrict__ va
       }
       if (live) {
         c[u] = __ldcs(col + o);
-        v[u] = ld_stream1(val + o);
+        v[u] = ld_stream1(PAT ? val + pattern_slot(val + o) : val + o);  // PAT: val holds the ones
       } else {
         c[u] = -1;
         v[u] = TV{};

@@ -75,8 +75,16 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
 #define PJDS_ROWS(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
 #define PJDS_PAT(RR, UU) dev::pjds_rows_kernel<TV, TX, IDX, RR, UU, SC, true><<<g, blk, 0, s>>>(PJDS_ARGS)
 #define PJDS_TPR(TT, UU) dev::pjds_tpr_kernel<TV, TX, IDX, TT, UU, SC><<<g, blk, 0, s>>>(PJDS_ARGS)
-  if (c.pattern) {
-    if (T != 1) return set_error(PJDS_EINVAL, "the pattern product runs one thread per row");
+#define PJDS_TPR_PAT(TT, UU) dev::pjds_tpr_kernel<TV, TX, IDX, TT, UU, SC, true><<<g, blk, 0, s>>>(PJDS_ARGS)
+  if (c.pattern && T > 1) {
+    if (U != 2 && U != 4) return set_error(PJDS_EINVAL, "unroll must be 2 or 4 with threads_per_row > 1");
+    switch (T) {
+      case 2: if (U == 2) PJDS_TPR_PAT(2, 2); else PJDS_TPR_PAT(2, 4); break;
+      case 4: if (U == 2) PJDS_TPR_PAT(4, 2); else PJDS_TPR_PAT(4, 4); break;
+      case 8: if (U == 2) PJDS_TPR_PAT(8, 2); else PJDS_TPR_PAT(8, 4); break;
+      default: return set_error(PJDS_EINVAL, "threads_per_row must be 1, 2, 4 or 8");
+    }
+  } else if (c.pattern) {
     if (R == 1 && U == 4) PJDS_PAT(1, 4);
     else if (R == 1 && U == 8) PJDS_PAT(1, 8);
     else if (R == 1 && U == 16) PJDS_PAT(1, 16);
@@ -113,6 +121,7 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
   }
 #undef PJDS_ROWS
 #undef PJDS_PAT
+#undef PJDS_TPR_PAT
 #undef PJDS_TPR
 #undef PJDS_ARGS
   return check_launch("pjds_spmv launch");
@@ -140,6 +149,15 @@ int launch_plan(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, cudaS
   d.n_diag = A->n_max + 1;
   d.reserved = 0;
   const int4 *plan = reinterpret_cast<const int4 *>(A->plan);
+  if (c.pattern) {  // the pattern kernel reads its values from eight ones
+    const cudaError_t e = dev::pattern_ones_address<TV>(&d.val);
+    if (e != cudaSuccess) return set_error(PJDS_ECUDA, "pattern values: %s", cudaGetErrorString(e));
+    if constexpr (std::is_same<TV, double>::value)
+      tiles::pjds_plan_kernel_f64<true><<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
+    else
+      tiles::pjds_plan_kernel<TV, TX, true><<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
+    return check_launch("pjds_spmv_pattern plan launch");
+  }
   if constexpr (std::is_same<TV, double>::value)
     tiles::pjds_plan_kernel_f64<><<<(unsigned)A->n_plan, tiles::BT, 0, s>>>(d, plan, A->n_pad);
   else

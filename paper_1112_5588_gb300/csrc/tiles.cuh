@@ -34,7 +34,10 @@ __device__ __forceinline__ void store_row(const Desc &d, TX *y, int64_t i, TA v)
   if (PJDS_IN(r, d.n_rows, dev::CHK_ROW)) y[r] = (TX)v;
 }
 
-template <typename TV, typename TX, typename IDX>
+// PAT (every routine below): the pattern product; d.val is then the address
+// of eight ones (dev::pattern_ones_address), read at
+// dev::pattern_slot(d.val + o) where the product reads d.val + o.
+template <typename TV, typename TX, typename IDX, bool PAT = false>
 __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int64_t i) {
   using TA = typename dev::Acc<TV>::T;
   constexpr int U = 4;
@@ -55,7 +58,7 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int6
       }
       if (live) {
         c[u] = __ldcs(d.col + o);
-        v[u] = dev::ld_stream1(val + o);
+        v[u] = dev::ld_stream1(PAT ? val + dev::pattern_slot(val + o) : val + o);
       } else {
         c[u] = -1;
         v[u] = TV{};
@@ -73,7 +76,7 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row(const Desc &d, int6
 // R adjacent sorted rows i .. i+R-1 (i a multiple of R: one block) with one
 // vector load of col and of val per jagged diagonal, U diagonals per round;
 // each row's arithmetic as in desc_row.
-template <typename TV, typename TX, typename IDX, int R, int U>
+template <typename TV, typename TX, typename IDX, int R, int U, bool PAT = false>
 __device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev::Acc<TV>::T (&acc)[R]) {
   using TA = typename dev::Acc<TV>::T;
   const TV *__restrict__ val = static_cast<const TV *>(d.val);
@@ -94,7 +97,10 @@ __device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev
       }
       if (live) {
         dev::ld_stream<R>(d.col + o, c[u]);
-        dev::ld_stream<R>(val + o, v[u]);
+        if constexpr (PAT)
+          dev::ld_stream<R>(val + dev::pattern_slot(val + o), v[u]);
+        else
+          dev::ld_stream<R>(val + o, v[u]);
       } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -118,16 +124,16 @@ __device__ __forceinline__ void desc_rows(const Desc &d, int64_t i, typename dev
 
 // R adjacent rows per thread from the tile's first row; rows past the tile
 // or the matrix are not stored.
-template <typename TV, typename TX, int R, int U>
+template <typename TV, typename TX, int R, int U, bool PAT = false>
 __device__ __forceinline__ void rows_tile(const Desc &d, const int4 &tl, TX *y) {
   const int32_t k = R * (int32_t)threadIdx.x;
   const int64_t i = (int64_t)tl.y + k;
   if (k >= tl.z || i >= d.n_rows) return;
   typename dev::Acc<TV>::T acc[R];
   if (d.idx64)
-    desc_rows<TV, TX, int64_t, R, U>(d, i, acc);
+    desc_rows<TV, TX, int64_t, R, U, PAT>(d, i, acc);
   else
-    desc_rows<TV, TX, int32_t, R, U>(d, i, acc);
+    desc_rows<TV, TX, int32_t, R, U, PAT>(d, i, acc);
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (k + r < tl.z && i + r < d.n_rows) store_row(d, y, i + r, acc[r]);
@@ -135,7 +141,7 @@ __device__ __forceinline__ void rows_tile(const Desc &d, const int4 &tl, TX *y) 
 
 // LANES consecutive lanes share sorted row i: lane s takes jagged diagonals
 // s, s + LANES, ...; the partial sums are added with shuffles (fixed tree).
-template <typename TV, typename TX, typename IDX, int LANES>
+template <typename TV, typename TX, typename IDX, int LANES, bool PAT = false>
 __device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d, int64_t i, int32_t s, bool active) {
   using TA = typename dev::Acc<TV>::T;
   constexpr int U = 4;
@@ -157,7 +163,7 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d
       }
       if (live) {
         c[u] = __ldcs(d.col + o);
-        v[u] = dev::ld_stream1(val + o);
+        v[u] = dev::ld_stream1(PAT ? val + dev::pattern_slot(val + o) : val + o);
       } else {
         c[u] = -1;
         v[u] = TV{};
@@ -176,38 +182,38 @@ __device__ __forceinline__ typename dev::Acc<TV>::T desc_row_lanes(const Desc &d
 
 // A tile of BT / LANES rows with LANES lanes each; the whole CTA stays for the
 // shuffles.
-template <typename TV, typename TX, int LANES>
+template <typename TV, typename TX, int LANES, bool PAT = false>
 __device__ __forceinline__ void lanes_tile(const Desc &d, const int4 &tl, TX *y) {
   const int32_t r = threadIdx.x / LANES, s = threadIdx.x % LANES;
   const int64_t i = (int64_t)tl.y + r;
   const bool active = r < tl.z && i < d.n_rows;
-  const auto acc = d.idx64 ? desc_row_lanes<TV, TX, int64_t, LANES>(d, i, s, active)
-                           : desc_row_lanes<TV, TX, int32_t, LANES>(d, i, s, active);
+  const auto acc = d.idx64 ? desc_row_lanes<TV, TX, int64_t, LANES, PAT>(d, i, s, active)
+                           : desc_row_lanes<TV, TX, int32_t, LANES, PAT>(d, i, s, active);
   if (active && s == 0) store_row(d, y, i, acc);
 }
 
 // One plan entry tl = {matrix, first sorted row, rows, kind} of matrix d, by
 // the whole CTA: kind 0 two rows per thread, 3 four rows per thread, 1 one
 // row per thread, 2 / 4 / 8 lanes per row.
-template <typename TV, typename TX>
+template <typename TV, typename TX, bool PAT = false>
 __device__ __forceinline__ void run_tile(const Desc &d, const int4 &tl) {
   TX *y = static_cast<TX *>(d.y);
   if (tl.w == 0) {
-    rows_tile<TV, TX, 2, 4>(d, tl, y);
+    rows_tile<TV, TX, 2, 4, PAT>(d, tl, y);
   } else if (tl.w == 3) {  // blocks of at most 2 entries (PlanRule::quad_max_len)
-    rows_tile<TV, TX, 4, 1>(d, tl, y);
+    rows_tile<TV, TX, 4, 1, PAT>(d, tl, y);
   } else if (tl.w == 1) {
     const int64_t i = (int64_t)tl.y + threadIdx.x;
     if ((int32_t)threadIdx.x < tl.z && i < d.n_rows) {
-      const auto acc = d.idx64 ? desc_row<TV, TX, int64_t>(d, i) : desc_row<TV, TX, int32_t>(d, i);
+      const auto acc = d.idx64 ? desc_row<TV, TX, int64_t, PAT>(d, i) : desc_row<TV, TX, int32_t, PAT>(d, i);
       store_row(d, y, i, acc);
     }
   } else if (tl.w == 2) {
-    lanes_tile<TV, TX, 2>(d, tl, y);
+    lanes_tile<TV, TX, 2, PAT>(d, tl, y);
   } else if (tl.w == 4) {
-    lanes_tile<TV, TX, 4>(d, tl, y);
+    lanes_tile<TV, TX, 4, PAT>(d, tl, y);
   } else {
-    lanes_tile<TV, TX, 8>(d, tl, y);
+    lanes_tile<TV, TX, 8, PAT>(d, tl, y);
   }
 }
 
@@ -230,22 +236,22 @@ __device__ __forceinline__ bool plan_entry_ok(const int4 &tl, int32_t n_pad) {
 // Per-tile mapping of one product: CTA k takes plan entry k. The entries are
 // ordered by their work per lane, largest first, so the block scheduler
 // starts the long tiles first and fills in with short ones.
-template <typename TV, typename TX>
+template <typename TV, typename TX, bool PAT = false>
 __global__ void __launch_bounds__(BT) pjds_plan_kernel(const Desc d, const int4 *__restrict__ plan, int32_t n_pad) {
   const int4 tl = plan[blockIdx.x];
   if (!plan_entry_ok(tl, n_pad)) return;
-  run_tile<TV, TX>(d, tl);
+  run_tile<TV, TX, PAT>(d, tl);
 }
 
 // fp64 values: bounded to six resident CTAs per SM (40 registers; unbounded
 // the instance takes 42, allocated as 48: five CTAs per SM). fp32 and bf16
 // stay unbounded (40 and 34 registers).
-template <int = 0>  // a template: instantiated only where it is launched
+template <bool PAT = false>  // a template: instantiated only where it is launched
 __global__ void __launch_bounds__(BT, 6)
     pjds_plan_kernel_f64(const Desc d, const int4 *__restrict__ plan, int32_t n_pad) {
   const int4 tl = plan[blockIdx.x];
   if (!plan_entry_ok(tl, n_pad)) return;
-  run_tile<double, double>(d, tl);
+  run_tile<double, double, PAT>(d, tl);
 }
 
 }  // namespace tiles

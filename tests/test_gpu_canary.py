@@ -70,8 +70,9 @@ def test_spmv_and_ellr_write_only_y(mods, dtype, permute):
                 torch.cuda.synchronize()
                 assert intact(torch, raw, A.n_rows, D.vec_dtype), (cfg, b, A.n_rows)
                 assert torch.isfinite(y.float()).all(), cfg
-            # the pattern product (one thread per row, both tile orders)
-            for cfg in (dict(threads_per_row=1), dict(threads_per_row=1, tile_order=1)):
+            # the pattern product (one thread per row in both tile orders, T threads per row, the plan)
+            for cfg in (dict(threads_per_row=1), dict(threads_per_row=1, tile_order=1), dict(threads_per_row=4),
+                        dict(plan=1)):
                 raw, y = guarded(torch, A.n_rows, D.vec_dtype)
                 pjds.pjds_spmv_pattern(D, x, y, **cfg)
                 torch.cuda.synchronize()
@@ -112,6 +113,9 @@ def test_permute_spmm_batch_write_only_their_outputs(mods):
         guards = [guarded(torch, M.n_rows, torch.float64) for M in mats]
         B = batch.Batch(devs, xs, [g[1] for g in guards], **kw)
         B.run(use_graph=True)
+        torch.cuda.synchronize()
+        assert all(intact(torch, raw, M.n_rows, torch.float64) for (raw, _), M in zip(guards, mats)), kw
+        B.run_pattern()
         torch.cuda.synchronize()
         assert all(intact(torch, raw, M.n_rows, torch.float64) for (raw, _), M in zip(guards, mats)), kw
         B.destroy()

@@ -91,7 +91,43 @@ def test_pattern_permuted_basis(P, oracle_lib):
     assert np.array_equal(y.cpu().numpy().view(np.uint64), want.view(np.uint64))
 
 
-@pytest.mark.parametrize("cfg", [dict(plan=1), dict(threads_per_row=2), dict(staged=1)])
+@pytest.mark.parametrize("cfg", [dict(plan=1), dict(threads_per_row=2), dict(threads_per_row=8, unroll=2)])
+@pytest.mark.parametrize("dtype", ["f64", "bf16"])
+def test_pattern_plan_and_lanes_within_bound(P, oracle_lib, cfg, dtype):
+    # several lanes per row change the summation order: the oracle's bound
+    import torch
+    A = synth.zipf_rows(70_000, s=2.0, len_max=512, seed=8)
+    D = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype).to_device("cuda")
+    x = synth.vector(A.n_cols, seed=25)
+    xd = x.astype(np.float32).astype(np.float64) if dtype != "f64" else x
+    y = torch.full((A.n_rows,), float("nan"), dtype=D.vec_dtype, device="cuda")
+    P.pjds_spmv_pattern(D, torch.from_numpy(xd).to("cuda", D.vec_dtype), y, **cfg)
+    torch.cuda.synchronize()
+    S = _ones(A)
+    check = parity.check_fp64 if dtype == "f64" else parity.check_fp32
+    r = check(y.double().cpu().numpy(), oracle_lib.crs_spmv(S, xd), oracle_lib.crs_absmv(S, xd), np.diff(A.row_ptr))
+    assert r["ok"], r
+
+
+def test_pattern_batch_within_bound(P, oracle_lib):
+    import torch
+    from paper_1112_5588_gb300 import batch
+    mats = [synth.zipf_rows(n, s=2.0, len_max=300, seed=30 + n % 7) for n in (20_000, 70_001, 5_003)]
+    devs = [P.pjds_create(M.n_rows, M.n_cols, M.row_ptr, M.col, M.val, b=32).to_device("cuda") for M in mats]
+    xs = [synth.vector(M.n_cols, seed=26 + k) for k, M in enumerate(mats)]
+    ys = [torch.full((M.n_rows,), float("nan"), dtype=torch.float64, device="cuda") for M in mats]
+    B = batch.Batch(devs, [torch.from_numpy(x).cuda() for x in xs], ys)
+    B.run_pattern()
+    torch.cuda.synchronize()
+    for M, x, y in zip(mats, xs, ys):
+        S = _ones(M)
+        r = parity.check_fp64(y.cpu().numpy(), oracle_lib.crs_spmv(S, x), oracle_lib.crs_absmv(S, x),
+                              np.diff(M.row_ptr))
+        assert r["ok"], r
+    B.destroy()
+
+
+@pytest.mark.parametrize("cfg", [dict(staged=1)])
 def test_pattern_rejects_other_mappings(P, cfg):
     import torch
     A = synth.zipf_rows(70_000, s=2.0, len_max=512, seed=8)
