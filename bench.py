@@ -46,8 +46,8 @@ L2_FLUSH_BYTES = 256 << 20
 # while the kernel's source (spmv_kernels.cuh) hashes to the recorded value and
 # the launch configuration is the recorded one.
 NCU_TRAFFIC = {
-    # profiles/pjds_rows_kernel_hmep6.2M_f64.md section 2: 1,192,178,176 B read + 22,811,136 B written per launch
-    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_214_989_312, "src": "ddf6213e1a8e128d",
+    # profiles/pjds_rows_kernel_hmep6.2M_f64.md section 2: 1,192,336,896 B read + 22,891,008 B written per launch
+    ("hmep_f64_pjds", 6_200_000): {"bytes": 1_215_227_904, "src": "a48f132773d1b136",
                                    "cfg": {"rows_per_thread": 1, "threads_per_row": 1, "block_threads": 256,
                                            "unroll": 4, "staged": 0, "index64": 0, "tile_order": 1,
                                            "plan": -1}},
