@@ -633,6 +633,12 @@ def precision_gpu_leg(torch, pjds, args, dev, flush):
             t = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv_cfg(D, xv, yv, **kw), 10, 3, flush))
             rep[f"spmv_{dt}{tag}"] = {"gbs": round(nb / t / 1e9, 1), "us": round(t * 1e6, 2),
                                       "frac_of_hbm": round(nb / t / 1e9 / hbm_peak()[0], 4)}
+            if not tag:  # the gather ceiling of the default launch
+                yq = torch.empty_like(yv)
+                tq = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv_pattern(D, xv, yq), 10, 3, flush))
+                rep[f"spmv_{dt}"]["gather_ceiling_us"] = round(tq * 1e6, 2)
+                rep[f"spmv_{dt}"]["frac_of_min_hbm_gather_ceiling"] = round(
+                    (nb / t) / min(hbm_peak()[0] * 1e9, nb / tq), 4)
     # pJDS in the original basis against ELLPACK-R on the same matrix (fp64)
     Ho = pjds.pjds_create(S.n_rows, S.n_cols, S.row_ptr, S.col, S.val, b=32, dtype="f64")
     Do = Ho.to_device(dev)
