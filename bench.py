@@ -994,7 +994,6 @@ def run_case(argv) -> int:
     ap.add_argument("--plan", type=int, default=0)
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
-    ap.add_argument("--prefetch", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=1234)
@@ -1037,7 +1036,7 @@ def run_case(argv) -> int:
         else:
             kw = dict(staged=1 if a.staged else 0, threads_per_row=a.threads_per_row,
                       rows_per_thread=a.rows_per_thread, tile_order=a.tile_order, plan=a.plan,
-                      unroll=a.unroll, block_threads=a.block_threads, prefetch=a.prefetch)
+                      unroll=a.unroll, block_threads=a.block_threads)
             run = (lambda: pjds.pjds_spmv_pattern(D, x, y, **kw)) if a.kind == "pattern" else (  # noqa: E731
                 lambda: pjds.pjds_spmv_cfg(D, x, y, **kw))
     for _ in range(a.warmup):

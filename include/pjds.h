@@ -262,9 +262,6 @@ typedef struct pjds_launch {
                        used automatically from 2^31 stored entries on) */
   int32_t tile_order; /* 0 automatic, 1 the traversal table, -1 sorted order */
   int32_t plan;       /* 0 automatic, 1 the per-tile mapping of A->plan, -1 a uniform mapping */
-  int32_t prefetch;   /* 1: each chunk prefetches the next chunk's column and value lines into L2
-                         (one thread per row, one or two rows per thread, unroll 4); 0: not */
-  int32_t reserved;   /* 0 */
 } pjds_launch;
 
 int pjds_spmv_cfg(const pjds_dev *A, const void *x, void *y, const pjds_launch *cfg, void *stream);

@@ -137,10 +137,6 @@ static int resolve_cfg(const pjds_dev *A, const pjds_launch *cfg, LaunchCfg &c) 
     if (cfg->block_threads) c.block_threads = cfg->block_threads;
     if (cfg->unroll) c.unroll = cfg->unroll;
     if (cfg->index64) c.index64 = 1;
-    if (cfg->prefetch < 0 || cfg->prefetch > 1 || cfg->reserved) return set_error(PJDS_EINVAL, "bad prefetch/reserved");
-    c.prefetch = cfg->prefetch;
-    if (c.prefetch && (cfg->plan == 1 || cfg->staged)) return set_error(PJDS_EINVAL, "prefetch runs a uniform mapping");
-    if (c.prefetch) c.plan = 0;
     if (cfg->tile_order < -1 || cfg->tile_order > 1) return set_error(PJDS_EINVAL, "tile_order must be -1, 0 or 1");
     if (cfg->tile_order == 1 && !A->tile_order) return set_error(PJDS_EINVAL, "tile_order = 1 but A->tile_order is NULL");
     if (cfg->tile_order) c.tile_order = cfg->tile_order == 1;
@@ -181,8 +177,6 @@ extern "C" int pjds_spmv_resolve(const pjds_dev *A, const pjds_launch *cfg, pjds
   out->index64 = c.index64;
   out->tile_order = c.tile_order ? 1 : -1;
   out->plan = c.plan ? 1 : -1;
-  out->prefetch = c.prefetch;
-  out->reserved = 0;
   return PJDS_OK;
 }
 

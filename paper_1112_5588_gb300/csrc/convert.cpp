@@ -134,7 +134,7 @@ using namespace pjds;
 
 extern "C" const char *pjds_last_error(void) { return g_msg; }
 
-extern "C" int32_t pjds_version(void) { return 6; }
+extern "C" int32_t pjds_version(void) { return 5; }
 
 extern "C" void pjds_abi_sizes(int32_t out[5]) {
   out[0] = (int32_t)sizeof(pjds_host);

@@ -257,9 +257,7 @@ __device__ __forceinline__ TX gather_n(const TX *__restrict__ x, int32_t c, int3
 // PAT: the pattern product (every stored value taken as 1, val not read):
 // the same column stream, x gathers, fused multiply-adds (by the ones of
 // pattern_ones, L1 hits) and y stores.
-// PF: at the start of each chunk, prefetch the next chunk's column and value
-// lines into L2 (more loads in flight without more registers).
-template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER, bool PAT = false, bool PF = false>
+template <typename TV, typename TX, typename IDX, int R, int U, bool SCATTER, bool PAT = false>
 __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col,
                                                         const int64_t *__restrict__ col_start,
                                                         const int32_t *__restrict__ block_len,
@@ -280,15 +278,6 @@ __global__ void __launch_bounds__(512) pjds_rows_kernel(const TV *__restrict__ v
   for (int32_t j = 0; j < L; j += U) {
     int32_t c[U][R];
     TV v[U][R];
-    if constexpr (PF) {
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (j + U + u < L) {
-          const IDX o = (IDX)__ldg(col_start + j + U + u) + (IDX)i0;
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(col + o)));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(val + o)));
-        }
-    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       bool live = j + u < L && PJDS_IN(j + u, PJDS_EXT(n_diag), CHK_DIAG);

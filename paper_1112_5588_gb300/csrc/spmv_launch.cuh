@@ -23,7 +23,6 @@ struct LaunchCfg {
   int tile_order;       // 1: tiles taken in A->tile_order
   int plan;             // 1: per-tile mapping of A->plan (the fields above do not apply)
   int pattern = 0;      // 1: the pattern product (values taken as 1, val not read)
-  int prefetch = 0;     // 1: prefetch the next chunk's lines into L2 (R = 1 or 2, U = 4)
 };
 
 // Launch-status helper: a launch error becomes PJDS_ECUDA with a message.
@@ -95,13 +94,6 @@ int launch_pjds_idx(const pjds_dev *A, const TX *x, TX *y, const LaunchCfg &c, c
     else if (R == 4 && U == 2) PJDS_PAT(4, 2);
     else if (R == 4 && U == 4) PJDS_PAT(4, 4);
     else return set_error(PJDS_EINVAL, "unroll %d is not available for %d rows per thread", U, R);
-  } else if (c.prefetch) {
-    if (T == 1 && R == 1 && U == 4)
-      dev::pjds_rows_kernel<TV, TX, IDX, 1, 4, SC, false, true><<<g, blk, 0, s>>>(PJDS_ARGS);
-    else if (T == 1 && R == 2 && U == 4)
-      dev::pjds_rows_kernel<TV, TX, IDX, 2, 4, SC, false, true><<<g, blk, 0, s>>>(PJDS_ARGS);
-    else
-      return set_error(PJDS_EINVAL, "prefetch needs one thread per row, one or two rows per thread, unroll 4");
   } else if (T == 1 && R == 1) {
     if (U == 4) PJDS_ROWS(1, 4);
     else if (U == 8) PJDS_ROWS(1, 8);

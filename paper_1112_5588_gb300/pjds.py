@@ -56,8 +56,7 @@ class _PjdsDevS(ctypes.Structure):
 
 class _LaunchS(ctypes.Structure):
     _fields_ = [("rows_per_thread", _i32), ("threads_per_row", _i32), ("block_threads", _i32), ("unroll", _i32),
-                ("staged", _i32), ("index64", _i32), ("tile_order", _i32), ("plan", _i32), ("prefetch", _i32),
-                ("reserved", _i32)]
+                ("staged", _i32), ("index64", _i32), ("tile_order", _i32), ("plan", _i32)]
 
 
 class _EllrHostS(ctypes.Structure):
@@ -304,16 +303,13 @@ def pjds_spmv(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=None) -> t
 
 def pjds_spmv_cfg(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, rows_per_thread: int = 0,
                   threads_per_row: int = 0, block_threads: int = 0, unroll: int = 0, staged: int = 0,
-                  index64: int = 0, tile_order: int = 0, plan: int = 0, prefetch: int = 0,
-                  stream=None) -> torch.Tensor:
+                  index64: int = 0, tile_order: int = 0, plan: int = 0, stream=None) -> torch.Tensor:
     """y = A x with an explicit kernel configuration (pjds_spmv_cfg).
     tile_order: 0 automatic, 1 traversal table, -1 sorted order; plan: 0
-    automatic, 1 the per-tile mapping, -1 a uniform mapping; prefetch: 1
-    prefetches the next chunk's lines into L2."""
+    automatic, 1 the per-tile mapping, -1 a uniform mapping."""
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan,
-                   prefetch, 0)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan)
     _check(_lib.pjds_spmv_cfg(ctypes.byref(A.struct), x.data_ptr(), y.data_ptr(), ctypes.byref(cfg),
                               _stream_ptr(stream)), "pjds_spmv_cfg")
     return y
@@ -325,7 +321,7 @@ def pjds_spmv_pattern(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=No
     _check_vec(x, A.n_cols, A.vec_dtype, "x")
     _check_vec(y, A.n_rows, A.vec_dtype, "y")
     keys = ("rows_per_thread", "threads_per_row", "block_threads", "unroll", "staged", "index64", "tile_order",
-            "plan", "prefetch")
+            "plan")
     c = _LaunchS(*[int(cfg.pop(k, 0)) for k in keys])
     if cfg:
         raise TypeError(f"unknown launch fields {sorted(cfg)}")
@@ -335,18 +331,16 @@ def pjds_spmv_pattern(A: PjdsDevice, x: torch.Tensor, y: torch.Tensor, stream=No
 
 
 def pjds_spmv_resolve(A, rows_per_thread: int = 0, threads_per_row: int = 0, block_threads: int = 0,
-                      unroll: int = 0, staged: int = 0, index64: int = 0, tile_order: int = 0, plan: int = 0,
-                      prefetch: int = 0) -> dict:
+                      unroll: int = 0, staged: int = 0, index64: int = 0, tile_order: int = 0, plan: int = 0) -> dict:
     """The launch configuration pjds_spmv_cfg would use (no launch). `A` is a
     PjdsDevice or a PjdsHost (only sizes and alignment are read)."""
     s = A.struct if isinstance(A, PjdsDevice) else _dev_struct_from_host(A)
-    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan,
-                   prefetch, 0)
+    cfg = _LaunchS(rows_per_thread, threads_per_row, block_threads, unroll, staged, index64, tile_order, plan)
     out = _LaunchS()
     _check(_lib.pjds_spmv_resolve(ctypes.byref(s), ctypes.byref(cfg), ctypes.byref(out)), "pjds_spmv_resolve")
     return {"rows_per_thread": out.rows_per_thread, "threads_per_row": out.threads_per_row,
             "block_threads": out.block_threads, "unroll": out.unroll, "staged": out.staged,
-            "index64": out.index64, "tile_order": out.tile_order, "plan": out.plan, "prefetch": out.prefetch}
+            "index64": out.index64, "tile_order": out.tile_order, "plan": out.plan}
 
 
 def pjds_check_word(clear: bool = True, stream=None) -> int:

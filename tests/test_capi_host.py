@@ -62,7 +62,7 @@ def test_create_shape_equals_create(P, b):
 
 
 def test_abi_version_and_struct_sizes(P):
-    assert P.lib().pjds_version() == 6  # the binding itself checked the struct sizes on load
+    assert P.lib().pjds_version() == 5  # the binding itself checked the struct sizes on load
 
 
 CASES = [
