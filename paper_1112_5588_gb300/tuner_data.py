@@ -245,7 +245,10 @@ def plan_eval(data: dict, rows, reps: int = 3, log=sys.stderr) -> dict:
     cands = json.loads(str(data["cands"]))
     params = json.loads(str(data["params"]))
     stored = data["times_us"]
-    ci = {(c["b"], c["dtype"], c["threads_per_row"]): k for k, c in enumerate(cands)}
+    # the uniform candidates in sorted order (the full candidate space also
+    # holds the traversal-table and per-tile entries)
+    ci = {(c["b"], c["dtype"], c["threads_per_row"]): k for k, c in enumerate(cands)
+          if c.get("plan", 0) != 1 and c.get("tile_order", 0) in (0, -1)}
     out = {"i": [], "n": []}
     for dt in DTYPES:
         out[f"{dt}_uniform_us"], out[f"{dt}_plan_us"], out[f"{dt}_rule_over_best"] = [], [], []
@@ -255,7 +258,7 @@ def plan_eval(data: dict, rows, reps: int = 3, log=sys.stderr) -> dict:
         lens = np.diff(A.row_ptr)
         test = []
         for dt in DTYPES:
-            idx = [c for c, cd in enumerate(cands) if cd["dtype"] == dt]
+            idx = [k for k in ci.values() if cands[k]["dtype"] == dt]
             best = min(idx, key=lambda c: stored[i, c])
             cand = {key: cands[best][key] for key in ("b", "dtype", "rows_per_thread", "threads_per_row",
                                                       "block_threads", "unroll", "staged")}
@@ -267,7 +270,7 @@ def plan_eval(data: dict, rows, reps: int = 3, log=sys.stderr) -> dict:
             u, p = entries[2 * j], entries[2 * j + 1]
             ok = u["status"] == 0 and p["status"] == 0
             t_rule = uniform_threads(A.n_rows, A.nnz, int(lens.max()), dt)
-            best_stored = np.nanmin([stored[i, c] for c, cd in enumerate(cands) if cd["dtype"] == dt])
+            best_stored = np.nanmin([stored[i, k] for k in ci.values() if cands[k]["dtype"] == dt])
             out[f"{dt}_uniform_us"].append(u["us"] if ok else np.nan)
             out[f"{dt}_plan_us"].append(p["us"] if ok else np.nan)
             out[f"{dt}_rule_over_best"].append(stored[i, ci[(32, dt, t_rule)]] / best_stored)
