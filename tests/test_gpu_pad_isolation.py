@@ -24,7 +24,6 @@ CONFIGS = [None, dict(threads_per_row=1), dict(threads_per_row=2), dict(threads_
            dict(plan=1), dict(staged=1)]
 
 
-
 def _spread(A, f):
     """The same rows with column c renamed f*c + 1: most columns unreferenced."""
     return A._replace(n_cols=A.n_cols * f + 1, col=(A.col.astype(np.int64) * f + 1).astype(np.int32))
