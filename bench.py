@@ -837,17 +837,22 @@ def batching_leg(torch, pjds, args, dev, flush):
 def tuning_leg(torch, pjds, args, dev):
     """The candidate sweep on the DLR-like matrix (long rows, fp32): the
     exhaustive autotuner's 36 candidates (b in 32..256, T in 1..8, sorted or
-    table tile order, the per-tile mapping) with the L2 flushed between runs,
-    against the paper's mapping (b = 32, one thread per row), the library's
-    default and the learned picker (pjds_tune_pick: the model inside its
-    training range, the sweep outside it)."""
+    table tile order, the per-tile mapping; rows per thread left to the
+    default rule) with the L2 flushed between runs, against the paper's
+    mapping (b = 32, one row per thread, sorted order, timed in the same
+    sweep), the library's default and the learned picker (pjds_tune_pick: the
+    model inside its training range, the sweep outside it)."""
     import synth
     from paper_1112_5588_gb300 import learned, tune, tuner_data
     A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=args.seed)
     cands = tune.default_space(("f32",))
-    entries, best = tune.sweep(A, cands, reps=5)
+    # the paper's mapping, timed in the same sweep: b = 32, one row per thread, sorted order
+    paper_cand = {"b": 32, "dtype": "f32", "rows_per_thread": 1, "threads_per_row": 1, "tile_order": -1, "plan": -1}
+    entries, best = tune.sweep(A, cands + [paper_cand], reps=5)
+    paper = round(entries[-1]["us"], 2)
+    entries = entries[:-1]
+    best = min((k for k, e in enumerate(entries) if e["status"] == 0), key=lambda k: entries[k]["us"])
     us = {tune.cand_key(c): round(e["us"], 2) for c, e in zip(cands, entries) if e["status"] == 0}
-    paper = us["b32_T1_sorted"]
     pick = learned.pick(A, "f32")
     t_pick = us[tune.cand_key(pick)]
     D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="f32").to_device(dev)
@@ -857,9 +862,13 @@ def tuning_leg(torch, pjds, args, dev):
     t_def = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv(D, x, y), 10, 3, flush)) * 1e6
     k_def = tuner_data.default_index(cands, A.n_rows, A.nnz, int(np.diff(A.row_ptr).max()), "f32")
     best_key = tune.cand_key(cands[best])
+    # candidates leave rows per thread to the default rule: on this block-structured
+    # matrix (pair_share 1000) the one-thread-per-row candidates pair rows like the default
+    rpt = {tune.cand_key(c): e["rows_per_thread"] for c, e in zip(cands, entries) if e["status"] == 0}
     return {"matrix": f"DLR-like N={A.n_rows} nnz={A.nnz} (144/row), fp32", "sweep_us": us,
-            "best": best_key, "best_us": us[best_key], "paper_mapping_us": paper,
-            "default_mapping": pjds.pjds_spmv_resolve(D), "default_us": round(t_def, 2),
+            "sweep_rows_per_thread": rpt, "best": best_key, "best_us": us[best_key], "paper_mapping_us": paper,
+            "default_mapping": pjds.pjds_spmv_resolve(D), "pair_share": D.pair_share, "default_us": round(t_def, 2),
+            "default_vs_sweep_best": round(t_def / us[best_key] - 1, 4),
             "default_in_sweep": tune.cand_key(cands[k_def]) if k_def >= 0 else None,
             "default_regret_in_sweep": round(us[tune.cand_key(cands[k_def])] / us[best_key] - 1, 4)
             if k_def >= 0 else None,

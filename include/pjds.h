@@ -89,6 +89,12 @@ void pjds_abi_sizes(int32_t out[5]);
  * per-tile mapping, the sorted rows cut into one-CTA tiles each mapped by its
  * block's length (see pjds_dev). It assumes 16-byte aligned device arrays;
  * the launcher checks.
+ * pair_share is a statistic of the matrix for the default mapping: the per
+ * mille of stored entries whose column equals the column of the paired row
+ * (sorted rows 2k and 2k + 1) at the same jagged diagonal, rounded down. It
+ * is high on block-structured matrices (rows of one block row share their
+ * columns), where one thread taking both rows of a pair reads each gathered x
+ * sector once for both.
  */
 typedef struct pjds_host {
   int32_t n_rows, n_cols, n_pad, b, n_blocks, n_max;
@@ -103,7 +109,8 @@ typedef struct pjds_host {
   void *val;          /* [n_stored] of dtype */
   int32_t *tile_order; /* [n_pad / 32] */
   int32_t *plan;       /* [4 * n_plan] per-tile mapping, see pjds_dev */
-  int32_t n_plan, plan_reserved;
+  int32_t n_plan;
+  int32_t pair_share; /* per mille, see below; 0 from pjds_create_shape */
 } pjds_host;
 
 /*
@@ -141,7 +148,8 @@ typedef struct pjds_dev {
   const void *val;
   const int32_t *tile_order; /* NULL: tiles in sorted order */
   const int32_t *plan;       /* NULL: no per-tile mapping */
-  int32_t n_plan, plan_reserved;
+  int32_t n_plan;
+  int32_t pair_share; /* copied from pjds_host (0: unknown); read by the default mapping only */
 } pjds_dev;
 
 /*
@@ -162,7 +170,8 @@ int pjds_create(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, const in
  * + 1]): the sort, padding, jagged-diagonal offsets, traversal table and
  * per-tile plan of pjds_create (original basis), every array equal to
  * pjds_create's for any columns and values with these row lengths, but col
- * and val are left NULL: the caller fills the n_stored entries itself (entry
+ * and val are left NULL and pair_share is 0: the caller fills the n_stored
+ * entries itself (entry
  * j of sorted row i, perm[i] being its original row, at col_start[j] + i for
  * j < row_len[i]; pads, up to the block length, column -1 and value +0), for
  * example directly in device memory when the CRS arrays would not fit the
@@ -197,10 +206,12 @@ int pjds_destroy(pjds_host *h);
  * below 64, else 8, then doubled (up to 8) while n_rows * T < 2^17. With
  * T = 1 each row sums in its original entry order; with T > 1 each lane sums
  * every T-th entry in order, then a fixed shuffle tree adds the T partial
- * sums. With one thread per row, fp32 and bf16 values from 2^21 rows on take
- * two adjacent rows per thread (same per-row arithmetic) when val and col
- * allow the paired loads. pjds_spmv_resolve reports the mapping chosen for a
- * matrix.
+ * sums. With one thread per row, fp32 and bf16 values take two adjacent
+ * rows per thread (same per-row arithmetic) when val and col allow the paired
+ * loads and either the matrix has at least 2^21 rows, or it has at least 2^18
+ * rows of at least 64 entries on average with pair_share >= 500 (the paired
+ * rows then share their x gathers). pjds_spmv_resolve reports the mapping
+ * chosen for a matrix.
  */
 int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
 

@@ -83,6 +83,14 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
 // from 2^21 rows on, when val and col are aligned for it, and every dtype
 // runs 256-thread CTAs: on the 27-point stencil (4.5M rows) bf16 162 -> 136
 // us, fp32 168 -> 160 us; on the HMEp-like matrix (6.2M rows) fp64 289 -> 283 us.
+// Pairs of rows also from 2^18 rows on when the paired rows share their
+// columns (pair_share >= 500: block-structured matrices) and rows hold 64
+// entries or more on average: the two rows' gathers of one jagged diagonal
+// then read the same x sector. Measured on block-dense matrices of 4x4 blocks
+// (64 and 144 entries per row, 280k to 1.1M rows) fp32 0.89-0.94 and bf16
+// 0.78-0.89 of the one-row time; below 2^18 rows (too few threads), with
+// 2x2 blocks of 40-entry rows (0.93-1.08), with fp64 values (0.98-1.33) or on
+// banded rows of 80-150 entries that share no columns (1.14-1.42) it does not pay.
 static int32_t default_threads_per_row(const pjds_dev *A) {
   const double entry = (double)(value_bytes(A->dtype) + 4);
   const double ratio = A->nnz > 0 ? (double)A->n_max * 1048576.0 / ((double)A->nnz * entry) : 0.0;
@@ -100,7 +108,9 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   if (t == 1) {
     c.block_threads = 256;
     const uintptr_t va = (uintptr_t)A->val, ca = (uintptr_t)A->col;
-    if (A->dtype != PJDS_F64 && A->n_rows >= (1 << 21) && va % (2 * value_bytes(A->dtype)) == 0 && ca % 8 == 0)
+    const bool paired = A->pair_share >= 500 && A->n_rows >= (1 << 18) && A->nnz >= 64 * (int64_t)A->n_rows;
+    if (A->dtype != PJDS_F64 && (A->n_rows >= (1 << 21) || paired) && va % (2 * value_bytes(A->dtype)) == 0 &&
+        ca % 8 == 0)
       c.rows_per_thread = 2;
   }
   c.unroll = 0;  // filled in by check_cfg once R and T are final

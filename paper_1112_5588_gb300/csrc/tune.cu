@@ -179,6 +179,7 @@ extern "C" int pjds_tune_sweep(int32_t n_rows, int32_t n_cols, const int64_t *ro
     d.tile_order = static_cast<const int32_t *>(place(h->tile_order, (size_t)(h->n_pad / 32) * 4));
     d.plan = static_cast<const int32_t *>(place(h->plan, (size_t)h->n_plan * 16));
     d.n_plan = h->n_plan;
+    d.pair_share = h->pair_share;
     void *x = p;
     p += a256((size_t)n_cols * 8);
     void *y = p;

@@ -44,14 +44,14 @@ class _PjdsHostS(ctypes.Structure):
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("inv_perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp),
                 ("col", _vp), ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32),
-                ("plan_reserved", _i32)]
+                ("pair_share", _i32)]
 
 
 class _PjdsDevS(ctypes.Structure):
     _fields_ = [("n_rows", _i32), ("n_cols", _i32), ("n_pad", _i32), ("b", _i32), ("n_blocks", _i32),
                 ("n_max", _i32), ("nnz", _i64), ("n_stored", _i64), ("dtype", _i32), ("permute_cols", _i32),
                 ("perm", _vp), ("block_len", _vp), ("row_len", _vp), ("col_start", _vp), ("col", _vp),
-                ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32), ("plan_reserved", _i32)]
+                ("val", _vp), ("tile_order", _vp), ("plan", _vp), ("n_plan", _i32), ("pair_share", _i32)]
 
 
 class _LaunchS(ctypes.Structure):
@@ -174,6 +174,8 @@ class PjdsHost:
         self.val = _np_view(s.val, s.n_stored, _VAL_NP[s.dtype])
         self.tile_order = _np_view(s.tile_order, s.n_pad // 32, np.int32)
         self.n_plan = int(s.n_plan)
+        # per mille of entries sharing the paired row's column (the default mapping's statistic)
+        self.pair_share = int(s.pair_share)
         # per-tile mapping: n_plan rows of (0, first sorted row, rows, kind)
         self.plan = _np_view(s.plan, 4 * s.n_plan, np.int32).reshape(-1, 4)
 
@@ -183,6 +185,7 @@ class PjdsHost:
         for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "col", "val", "tile_order", "plan"):
             out[k] = getattr(self, k).copy()
         out["n_plan"] = self.n_plan
+        out["pair_share"] = self.pair_share
         return out
 
     def to_device(self, device="cuda", tile_order: bool = True, plan: bool = True) -> "PjdsDevice":
@@ -274,6 +277,8 @@ class PjdsDevice:
         s.tile_order = (self.tile_order.data_ptr() or None) if tile_order else None
         s.plan = self.plan.data_ptr() if self.plan is not None else None
         s.n_plan = self.n_plan if self.plan is not None else 0
+        s.pair_share = host.pair_share
+        self.pair_share = host.pair_share
         self._s = s
 
     @property
@@ -372,6 +377,7 @@ def _dev_struct_from_host(H: "PjdsHost"):
     s.tile_order = 512 if len(H.tile_order) else None
     s.plan = 512 if H.n_plan else None
     s.n_plan = H.n_plan
+    s.pair_share = H.pair_share
     return s
 
 

@@ -55,6 +55,7 @@ def test_create_shape_equals_create(P, b):
             for k in ("perm", "inv_perm", "block_len", "row_len", "col_start", "tile_order", "plan"):
                 assert np.array_equal(getattr(S, k), getattr(H, k)), k
             assert len(S.col) == 0 and len(S.val) == 0
+            assert S.pair_share == 0  # no columns to compare
             H.destroy()
             S.destroy()
     with pytest.raises(P.PjdsError):
@@ -62,7 +63,7 @@ def test_create_shape_equals_create(P, b):
 
 
 def test_abi_version_and_struct_sizes(P):
-    assert P.lib().pjds_version() == 5  # the binding itself checked the struct sizes on load
+    assert P.lib().pjds_version() == 6  # the binding itself checked the struct sizes on load
 
 
 CASES = [
@@ -495,3 +496,64 @@ def test_check_word_only_in_the_checked_build(P):
     assert P.lib().pjds_check_word(ctypes.byref(w), 0, None) == -1
     assert b"checked build" in P.lib().pjds_last_error()
     assert w.value == 123 or w.value == 0
+
+
+def _pair_share(A, perm):
+    """Per mille of entries equal to the paired sorted row's entry at the same
+    position (rows perm[2k], perm[2k+1]), counted for both rows, rounded down."""
+    lens = np.diff(A.row_ptr)
+    matches = 0
+    for k in range(A.n_rows // 2):
+        a, c = perm[2 * k], perm[2 * k + 1]
+        m = min(lens[a], lens[c])
+        matches += int(np.sum(A.col[A.row_ptr[a]:A.row_ptr[a] + m] == A.col[A.row_ptr[c]:A.row_ptr[c] + m]))
+    return (2000 * matches) // max(int(A.row_ptr[-1]), 1)
+
+
+def test_pair_share(P):
+    # hand-worked: rows of lengths 2, 2, 1, 1 (sorted order = original order);
+    # rows 0 / 1 share column 0 at position 0, rows 2 / 3 share column 5:
+    # 2 matches, counted for both rows, of 6 entries -> 666 per mille
+    row_ptr = np.array([0, 2, 4, 5, 6], np.int64)
+    col = np.array([0, 3, 0, 4, 5, 5], np.int32)
+    H = P.pjds_create(4, 6, row_ptr, col, np.ones(6), b=32)
+    assert H.pair_share == 666
+    # an odd last row has no pair; an empty matrix has no entries
+    H = P.pjds_create(3, 6, row_ptr[:4], col[:5], np.ones(5), b=32)
+    assert H.pair_share == 2000 * 1 // 5
+    assert P.pjds_create(5, 3, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0), b=32).pair_share == 0
+    # block-structured rows share every column with their pair; the others barely
+    for A, lo, hi in ((synth.block_dense(2_000, 4, 36, 0.05, seed=2), 1000, 1000),
+                      (synth.block_dense(2_000, 2, 20, 0.05, seed=2), 1000, 1000),
+                      (synth.hmep_like(n=40_000, seed=3), 0, 100),
+                      (synth.banded_uniform(n=20_000, seed=3), 0, 100),
+                      (synth.zipf_rows(30_000, s=2.0, len_max=300, seed=4), 0, 300)):
+        for pc in (0, 1):
+            if pc and A.n_rows != A.n_cols:
+                continue
+            H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, permute_cols=pc)
+            want = _pair_share(A, H.perm)
+            assert H.pair_share == want and lo <= want <= hi, (H.pair_share, want)
+
+
+def test_resolve_pairs_rows_on_block_structured_matrices(P):
+    # fp32 / bf16 take two rows per thread from 2^18 rows of >= 64 entries on
+    # when paired rows share their columns; fp64, smaller matrices and
+    # unshared long rows keep one row per thread
+    D = synth.block_dense(70_000, 4, 36, 0.05, seed=2)  # 280k rows of 144, pair_share 1000
+    for dt, R in (("f64", 1), ("f32", 2), ("bf16", 2)):
+        H = P.pjds_create(D.n_rows, D.n_cols, D.row_ptr, D.col, D.val, b=32, dtype=dt)
+        r = P.pjds_spmv_resolve(H)
+        assert (r["threads_per_row"], r["rows_per_thread"], r["plan"]) == (1, R, -1), (dt, r)
+        s = P._dev_struct_from_host(H)
+        s.pair_share = 499
+        out = P._LaunchS()
+        assert P.lib().pjds_spmv_resolve(ctypes.byref(s), None, ctypes.byref(out)) == 0
+        assert out.rows_per_thread == 1
+        H.destroy()
+    D2 = synth.block_dense(35_000, 4, 36, 0.05, seed=2)  # 140k rows
+    H = P.pjds_create(D2.n_rows, D2.n_cols, D2.row_ptr, D2.col, D2.val, b=32, dtype="f32")
+    assert P.pjds_spmv_resolve(H)["rows_per_thread"] == 1
+    B = synth.banded_uniform(n=300_000, m_lo=60, m_hi=100, hw=2000, seed=3)  # long rows, nothing shared
+    H = P.pjds_create(B.n_rows, B.n_cols, B.row_ptr, B.col, B.val, b=32, dtype="f32")
+    assert H.pair_share < 100 and P.pjds_spmv_resolve(H)["rows_per_thread"] == 1
