@@ -200,3 +200,30 @@ def test_stencil_lanczos_f32_ritz_refined_full(P, oracle_lib, stencil):
         del V
         torch.cuda.empty_cache()
     assert thetas[1] == pytest.approx(thetas[0], rel=1e-10)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_dlr_default_paired_rows_full(P, oracle_lib, dtype):
+    # the single product on the DLR-like matrix (280k rows of 144, 4x4 blocks):
+    # the default pairs rows (pair_share 1000); every element within the fp32
+    # bound of the oracle and bit for bit the one-row-per-thread product
+    import torch
+    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=1234)
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype)
+    assert H.pair_share == 1000
+    D = H.to_device("cuda")
+    H.destroy()
+    assert P.pjds_spmv_resolve(D)["rows_per_thread"] == 2
+    x = synth.vector(A.n_cols, seed=31).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.full((A.n_rows,), float("nan"), device="cuda")
+    P.pjds_spmv(D, xt, y)
+    y1 = torch.full((A.n_rows,), float("nan"), device="cuda")
+    P.pjds_spmv_cfg(D, xt, y1, rows_per_thread=1, threads_per_row=1)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y1)
+    Ar = A._replace(val=oracle_lib.round_f32(A.val) if dtype == "f32" else oracle_lib.round_bf16(A.val))
+    xd = x.astype(np.float64)
+    r = parity.check_fp32(y.double().cpu().numpy(), oracle_lib.crs_spmv(Ar, xd), oracle_lib.crs_absmv(Ar, xd),
+                          np.diff(A.row_ptr))
+    assert r["ok"], r
