@@ -210,8 +210,8 @@ int pjds_destroy(pjds_host *h);
  * rows per thread (same per-row arithmetic) when val and col allow the paired
  * loads and either the matrix has at least 2^21 rows, or it has at least 2^18
  * rows of at least 64 entries on average with pair_share >= 500 (the paired
- * rows then share their x gathers). pjds_spmv_resolve reports the mapping
- * chosen for a matrix.
+ * rows then share their x gathers; 128-thread CTAs in that case).
+ * pjds_spmv_resolve reports the mapping chosen for a matrix.
  */
 int pjds_spmv(const pjds_dev *A, const void *x, void *y, void *stream);
 

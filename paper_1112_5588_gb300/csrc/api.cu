@@ -88,7 +88,8 @@ static int check_cfg(const pjds_dev *A, LaunchCfg &c) {
 // entries or more on average: the two rows' gathers of one jagged diagonal
 // then read the same x sector. Measured on block-dense matrices of 4x4 blocks
 // (64 and 144 entries per row, 280k to 1.1M rows) fp32 0.89-0.94 and bf16
-// 0.78-0.89 of the one-row time; below 2^18 rows (too few threads), with
+// 0.78-0.89 of the one-row time, on 128-thread CTAs (1-7% faster than 256
+// there: the halved thread count spreads over more CTAs per SM); below 2^18 rows (too few threads), with
 // 2x2 blocks of 40-entry rows (0.93-1.08), with fp64 values (0.98-1.33) or on
 // banded rows of 80-150 entries that share no columns (1.14-1.42) it does not pay.
 static int32_t default_threads_per_row(const pjds_dev *A) {
@@ -110,8 +111,10 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
     const uintptr_t va = (uintptr_t)A->val, ca = (uintptr_t)A->col;
     const bool paired = A->pair_share >= 500 && A->n_rows >= (1 << 18) && A->nnz >= 64 * (int64_t)A->n_rows;
     if (A->dtype != PJDS_F64 && (A->n_rows >= (1 << 21) || paired) && va % (2 * value_bytes(A->dtype)) == 0 &&
-        ca % 8 == 0)
+        ca % 8 == 0) {
       c.rows_per_thread = 2;
+      if (paired) c.block_threads = 128;  // half the threads: spread over more CTAs
+    }
   }
   c.unroll = 0;  // filled in by check_cfg once R and T are final
   c.staged = 0;

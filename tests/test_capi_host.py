@@ -545,6 +545,7 @@ def test_resolve_pairs_rows_on_block_structured_matrices(P):
         H = P.pjds_create(D.n_rows, D.n_cols, D.row_ptr, D.col, D.val, b=32, dtype=dt)
         r = P.pjds_spmv_resolve(H)
         assert (r["threads_per_row"], r["rows_per_thread"], r["plan"]) == (1, R, -1), (dt, r)
+        assert r["block_threads"] == (128 if R == 2 else 256), (dt, r)
         s = P._dev_struct_from_host(H)
         s.pair_share = 499
         out = P._LaunchS()
