@@ -129,8 +129,11 @@ typedef struct pjds_host {
  * rows' block: 8 lanes per row from 256 entries, 4 from 64, 2 from 16 (kinds
  * 8, 4, 2; 256 / lanes rows), else two adjacent rows per thread (kind 0, 512
  * rows) or four for blocks of at most 2 entries (kind 3, 1024 rows); a tile
- * ends where the kind changes, and the entries are ordered by work per lane,
- * largest first. A row gives the same bits as with the same lanes per row in
+ * ends where the kind changes. The entries are ordered by work per lane,
+ * largest first; from 2^21 rows on, the entries of kinds 0 and 3 then follow
+ * the others in the order of the original index of their first row (perm of
+ * its first sorted row), so that the short rows in flight lie close together
+ * in the original numbering. A row gives the same bits as with the same lanes per row in
  * the uniform mappings (one thread per row for kinds 0 and 3). The plan
  * kernel runs one CTA per entry; it needs plan, val and col 16-byte aligned
  * and skips an entry that does not describe a tile of the matrix.

@@ -282,11 +282,22 @@ static int create_impl(int32_t n_rows, int32_t n_cols, const int64_t *row_ptr, c
 
   // per-tile mapping: tiles of the default rule (pair and quad kinds assume
   // 16-byte aligned device arrays; the launcher checks), by work per lane,
-  // largest first (stable)
+  // largest first (stable). From 2^21 rows on, the tiles of two or four short
+  // rows per thread then move behind the others, in the original order of
+  // their first rows: the short rows in flight at any moment lie close
+  // together in the original numbering, and their scattered y stores fill
+  // whole sectors before the lines leave L2, which the vectors no longer fit
+  // beside the streams (smaller matrices gain nothing from it)
   {
     std::vector<PlanTile> cut;
     plan_cut(n_rows, b, h->block_len, k_plan_rule, 0, true, true, cut);
     std::stable_sort(cut.begin(), cut.end(), [](const PlanTile &a, const PlanTile &c) { return a.cost > c.cost; });
+    if (n_rows >= k_plan_first_row_order_min_rows) {
+      const auto long_rows = [](const PlanTile &t) { return t.kind != KIND_PAIR && t.kind != KIND_QUAD; };
+      const auto tail = std::stable_partition(cut.begin(), cut.end(), long_rows);
+      std::stable_sort(tail, cut.end(),
+                       [&](const PlanTile &a, const PlanTile &c) { return perm[a.row0] < perm[c.row0]; });
+    }
     h->n_plan = (int32_t)cut.size();
     h->plan = alloc_n<int32_t>(4 * std::max<int64_t>((int64_t)cut.size(), 1));
     if (!h->plan) {

@@ -32,6 +32,8 @@ struct PlanRule {
 // took the batched launch from 253 to 237 us in fp64 (241 -> 214 us fp32)
 // against two rows per thread, with the same bits.
 constexpr PlanRule k_plan_rule = {{16, 64, 256}, 2};
+// rows from which pjds_create orders a product's short-row tiles by first original row
+constexpr int32_t k_plan_first_row_order_min_rows = 1 << 21;
 
 struct PlanTile {
   int32_t row0, rows, kind;

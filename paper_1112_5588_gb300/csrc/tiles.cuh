@@ -235,7 +235,9 @@ __device__ __forceinline__ bool plan_entry_ok(const int4 &tl, int32_t n_pad) {
 
 // Per-tile mapping of one product: CTA k takes plan entry k. The entries are
 // ordered by their work per lane, largest first, so the block scheduler
-// starts the long tiles first and fills in with short ones.
+// starts the long tiles first (on large matrices the short-row entries follow
+// in the original order of their first rows). Any order gives the same
+// results.
 template <typename TV, typename TX, bool PAT = false>
 __global__ void __launch_bounds__(BT) pjds_plan_kernel(const Desc d, const int4 *__restrict__ plan, int32_t n_pad) {
   const int4 tl = plan[blockIdx.x];

@@ -443,13 +443,32 @@ def test_plan_definition(P, make, b):
     for (row0, rows, kind), nxt in zip(by_row[:, 1:], list(by_row[1:, 1:]) + [None]):
         if rows < PLAN_CAP[int(kind)] and nxt is not None:
             assert nxt[2] != kind or _plan_kind(int(bl[(row0 + rows) // b])) != kind
-    # entries by work per lane, largest first
-    def cost(row0, rows, kind):
-        lanes = 1 if kind in (0, 3) else kind
-        blocks = np.arange(row0, row0 + rows) // b
-        return int(bl[blocks].astype(np.int64).sum()) // lanes
-    costs = [cost(*map(int, e[1:])) for e in plan]
+    # entries by work per lane, largest first (below 2^21 rows)
+    costs = [_plan_cost(bl, b, *map(int, e[1:])) for e in plan]
     assert all(c0 >= c1 for c0, c1 in zip(costs, costs[1:]))
+
+
+def _plan_cost(bl, b, row0, rows, kind):
+    lanes = 1 if kind in (0, 3) else kind
+    blocks = np.arange(row0, row0 + rows) // b
+    return int(bl[blocks].astype(np.int64).sum()) // lanes
+
+
+def test_plan_order_from_2_21_rows(P):
+    # from 2^21 rows: the entries of several lanes per row first, by work per
+    # lane, largest first; then the short-row entries (kinds 0 and 3) by the
+    # original index of their first row
+    Z = synth.zipf_rows(1 << 21, s=2.0, len_max=512, seed=5)
+    H = P.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
+    plan, bl = H.plan, H.block_len
+    short = np.isin(plan[:, 3], (0, 3))
+    n_long = int((~short).sum())
+    assert 0 < n_long < len(plan)
+    assert not short[:n_long].any() and short[n_long:].all()
+    costs = [_plan_cost(bl, 32, *map(int, e[1:])) for e in plan[:n_long]]
+    assert all(c0 >= c1 for c0, c1 in zip(costs, costs[1:]))
+    first = H.perm[plan[n_long:, 1]]
+    assert np.all(first[:-1] < first[1:])
 
 
 def test_plan_resolve(P):
