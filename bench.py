@@ -764,8 +764,23 @@ def batching_leg(torch, pjds, args, dev, flush):
         spmm[f"k{k}"]["gathered_bytes_per_entry"] = 4 * k
     spmm["ceiling_note"] = ("frac_of_gather_ceiling = pattern-product time / product time: the pattern product "
                             "(pjds_spmm_pattern) is the same launch without reading the values")
+    spmm["pair_share"] = D.pair_share
+    # bf16 values (fp32 vectors): one thread per pair of rows sharing their columns from k = 8
+    Hb = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype="bf16")
+    Db = Hb.to_device(dev)
+    Hb.destroy()
+    spmm["bf16"] = {}
+    for k in (8, 32):
+        X = torch.rand(A.n_cols, k, device=dev)
+        Y = torch.empty(A.n_rows, k, device=dev)
+        t = statistics.median(time_launches(torch, lambda: batch.spmm(Db, X, Y), 10, 3, flush))
+        tp = statistics.median(time_launches(torch, lambda: batch.spmm_pattern(Db, X, Y), 10, 3, flush))
+        nb = A.nnz * 6 + 4 * k * (A.n_cols + A.n_rows) + 4 * A.n_rows
+        spmm["bf16"][f"k{k}"] = {"us": round(t * 1e6, 2), "gbs": round(nb / t / 1e9, 1),
+                                 "gflops": round(2 * A.nnz * k / t / 1e9, 1),
+                                 "gather_ceiling_us": round(tp * 1e6, 2), "frac_of_gather_ceiling": round(tp / t, 4)}
     out["spmm"] = spmm
-    del D
+    del D, Db
     rng = np.random.default_rng(args.seed)
     sizes = np.exp(rng.uniform(np.log(10_000), np.log(500_000), 64)).astype(int)
     from paper_1112_5588_gb300 import learned
@@ -991,7 +1006,8 @@ def run_case(argv) -> int:
     ap.add_argument("--n", type=int, default=2_000_000)
     ap.add_argument("--g", type=int, default=100)
     ap.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
-    ap.add_argument("--kind", choices=["spmv", "pattern", "ellr", "spmm", "cg", "lanczos", "batch", "mlp"],
+    ap.add_argument("--kind", choices=["spmv", "pattern", "ellr", "spmm", "spmm_pattern", "cg", "lanczos", "batch",
+                                       "mlp"],
                     default="spmv")
     ap.add_argument("--mats", type=int, default=64)
     ap.add_argument("--k", type=int, default=8)
@@ -1033,10 +1049,11 @@ def run_case(argv) -> int:
     else:
         D = pjds.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=a.dtype,
                              permute_cols=a.permuted).to_device(dev)
-    if a.kind == "spmm":
+    if a.kind in ("spmm", "spmm_pattern"):
         X = torch.rand(A.n_cols, a.k, device=dev, dtype=D.vec_dtype)
         Y = torch.empty(A.n_rows, a.k, device=dev, dtype=D.vec_dtype)
-        run = lambda: batch.spmm(D, X, Y)  # noqa: E731
+        fn = batch.spmm if a.kind == "spmm" else batch.spmm_pattern
+        run = lambda: fn(D, X, Y)  # noqa: E731
     else:
         x = torch.from_numpy(synth.vector(A.n_cols, seed=a.seed)).to(dev, D.vec_dtype)
         y = torch.empty(A.n_rows, device=dev, dtype=D.vec_dtype)

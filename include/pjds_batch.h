@@ -29,9 +29,14 @@ extern "C" {
  * row and 16 or 32 bytes of its k columns (32 when that leaves at least two
  * threads per row, the rows are not widely spread in length and the launch
  * still has 2^19 threads), so the lanes of a row read each gathered row of X
- * as one contiguous segment. Column c of Y is computed in
- * the same order and with the same fused multiply-adds as pjds_spmv with one
- * thread per row on column c of X. Original basis (permute_cols = 0): row i of
+ * as one contiguous segment. On block-structured matrices (pair_share >= 500,
+ * at least 2^18 rows of 64 entries or more on average; see pjds_host) with
+ * bf16 values and k a multiple of 8, or fp32 values and k = 8 or a multiple of
+ * 8 from 64 on, each thread takes both rows of a pair of adjacent sorted rows
+ * and 32 bytes of their columns, and one gathered segment of X serves both
+ * rows where their columns agree. Column c of Y is
+ * computed in the same order and with the same fused multiply-adds as
+ * pjds_spmv with one thread per row on column c of X. Original basis (permute_cols = 0): row i of
  * the sorted matrix is written to row perm[i] of Y; permuted basis: to row i.
  */
 int pjds_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, void *stream);

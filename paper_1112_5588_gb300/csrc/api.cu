@@ -109,7 +109,7 @@ static LaunchCfg default_cfg(const pjds_dev *A) {
   if (t == 1) {
     c.block_threads = 256;
     const uintptr_t va = (uintptr_t)A->val, ca = (uintptr_t)A->col;
-    const bool paired = A->pair_share >= 500 && A->n_rows >= (1 << 18) && A->nnz >= 64 * (int64_t)A->n_rows;
+    const bool paired = shared_pairs(A);
     if (A->dtype != PJDS_F64 && (A->n_rows >= (1 << 21) || paired) && va % (2 * value_bytes(A->dtype)) == 0 &&
         ca % 8 == 0) {
       c.rows_per_thread = 2;

@@ -118,6 +118,124 @@ __global__ void __launch_bounds__(BT)
     V16<TX>::store(Y + r * k + (int64_t)q * W + h * VW, *reinterpret_cast<const TX(*)[VW]>(&out[h * VW]));
 }
 
+// The pattern product's value address reduced to a slot of the ones (0 for
+// every address the product reads), opaque to the compiler like
+// dev::pattern_slot but without a volatile asm: a volatile statement also
+// fixes its place in the schedule, which kept the paired kernel's loads of a
+// round from interleaving (its pattern product of bf16 values at k = 32 ran
+// 16% slower than the product itself).
+template <typename TV>
+__device__ __forceinline__ int pair_pattern_slot(const TV *p) {
+  asm("" : "+l"(p));
+  return (int)(reinterpret_cast<uintptr_t>(p) & 3);
+}
+
+// Two of the pattern product's ones, through L1 with the normal eviction priority.
+__device__ __forceinline__ void ld_ones2(const double *p, double (&v)[2]) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  v[0] = a.x, v[1] = a.y;
+}
+__device__ __forceinline__ void ld_ones2(const float *p, float (&v)[2]) {
+  const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+  v[0] = a.x, v[1] = a.y;
+}
+__device__ __forceinline__ void ld_ones2(const dev::bf16_t *p, dev::bf16_t (&v)[2]) {
+  const unsigned int a = __ldg(reinterpret_cast<const unsigned int *>(p));
+  v[0].bits = (uint16_t)(a & 0xFFFFu);
+  v[1].bits = (uint16_t)(a >> 16);
+}
+
+// Paired rows: thread t takes sorted rows 2p and 2p + 1 (p = t / lr) and the
+// same CH chunks of their k columns as spmm_kernel. Where the two rows have
+// the same column at a jagged diagonal (block-structured matrices), one
+// gather of the X row serves both; otherwise row 2p + 1 gathers its own.
+// Each row sums in the order and with the fused multiply-adds of
+// spmm_kernel. Row 2p is at least as long as row 2p + 1 (sorted order), so
+// a pad of the first is a pad of the second.
+template <typename TV, typename TX, typename IDX, bool SCATTER, int CH, int U, bool PAT = false>
+__global__ void __launch_bounds__(BT)
+    spmm_pair_kernel(const TV *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ col_start,
+                     const int32_t *__restrict__ block_len, const int32_t *__restrict__ perm, const TX *__restrict__ X,
+                     TX *__restrict__ Y, int32_t n_rows, int32_t b, int32_t k, int32_t lr) {
+  using TA = typename dev::Acc<TV>::T;
+  constexpr int VW = V16<TX>::W, W = VW * CH;
+  const int64_t t = (int64_t)blockIdx.x * BT + threadIdx.x;
+  const int64_t i = 2 * (t / lr);
+  const int32_t q = (int32_t)(t % lr);
+  if (i >= n_rows) return;
+  const int32_t L = PJDS_IN(i / b, PJDS_EXT(n_blocks), dev::CHK_BLOCK) ? __ldg(block_len + (int32_t)(i / b)) : 0;
+  TA acc0[W], acc1[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc0[w] = acc1[w] = TA(0);
+  for (int32_t j = 0; j < L; j += U) {
+    int32_t c[U][2];
+    TV v[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      bool live = j + u < L && PJDS_IN(j + u, PJDS_EXT(n_diag), dev::CHK_DIAG);
+      IDX o = 0;
+      if (live) {
+        o = (IDX)__ldg(col_start + j + u) + (IDX)i;
+        live = PJDS_IN(o, PJDS_EXT(stored), dev::CHK_OFFSET) && PJDS_IN((int64_t)o + 1, PJDS_EXT(stored), dev::CHK_OFFSET);
+      }
+      if (live) {
+        dev::ld_stream<2>(col + o, c[u]);
+        if constexpr (PAT)
+          ld_ones2(val + pair_pattern_slot(val + o), v[u]);  // val holds the ones
+        else
+          dev::ld_stream<2>(val + o, v[u]);
+      } else {
+        c[u][0] = c[u][1] = -1;
+        v[u][0] = v[u][1] = TV{};
+      }
+    }
+    TX xv[U][W];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (c[u][0] >= 0 && PJDS_IN(c[u][0], PJDS_EXT(n_cols), dev::CHK_COLUMN)) {
+#pragma unroll
+        for (int h = 0; h < CH; ++h)
+          V16<TX>::load(X + (int64_t)c[u][0] * k + (int64_t)q * W + h * VW,
+                        *reinterpret_cast<TX(*)[VW]>(&xv[u][h * VW]));
+      } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) xv[u][w] = TX(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+        acc0[w] = c[u][0] >= 0 ? dev::fma_acc(dev::to_acc(v[u][0]), (TA)xv[u][w], acc0[w]) : acc0[w];
+      if (c[u][1] == c[u][0]) {
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+          acc1[w] = c[u][1] >= 0 ? dev::fma_acc(dev::to_acc(v[u][1]), (TA)xv[u][w], acc1[w]) : acc1[w];
+      } else if (c[u][1] >= 0 && PJDS_IN(c[u][1], PJDS_EXT(n_cols), dev::CHK_COLUMN)) {
+        TX x1[W];
+#pragma unroll
+        for (int h = 0; h < CH; ++h)
+          V16<TX>::load(X + (int64_t)c[u][1] * k + (int64_t)q * W + h * VW, *reinterpret_cast<TX(*)[VW]>(&x1[h * VW]));
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc1[w] = dev::fma_acc(dev::to_acc(v[u][1]), (TA)x1[w], acc1[w]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int64_t ir = i + r;
+    if (ir >= n_rows) break;
+    TX out[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) out[w] = (TX)(r == 0 ? acc0[w] : acc1[w]);
+    const int64_t row = SCATTER ? (int64_t)__ldcs(perm + ir) : ir;
+    if (!PJDS_IN(row, PJDS_EXT(n_rows), dev::CHK_ROW)) continue;
+#pragma unroll
+    for (int h = 0; h < CH; ++h)
+      V16<TX>::store(Y + row * k + (int64_t)q * W + h * VW, *reinterpret_cast<const TX(*)[VW]>(&out[h * VW]));
+  }
+}
+
 // ----------------------------------------------------------------------------- persistent batch
 
 using namespace pjds::tiles;
@@ -202,7 +320,12 @@ struct pjds_batch {
 // faster than one chunk), one chunk when the longest row has more than 4
 // times the mean length (the longest rows' latency then sets the time and
 // more lanes per row help) or otherwise. Four chunks were within 4% of two
-// at best and are not built.
+// at best and are not built. Paired rows (shared_pairs: block-structured
+// matrices, fp32 / bf16, k >= 8) run spmm_pair_kernel with two chunks:
+// DLR-like matrices of 280k and 560k rows, against spmm_kernel, bf16
+// 0.57-0.73 of the time (k = 8..64), fp32 0.85-0.92 at k = 8 and 0.87-0.94
+// at k = 64, but 0.98-1.03 at k = 16 and 32 (not paired there); one chunk
+// per lane, or fp64 values (bound by the fp64 pipe), gained nothing.
 static int spmm_chunks(const pjds_dev *A, int32_t k, int vw) {
   if ((int64_t)A->n_max * A->n_rows > 4 * A->nnz) return 1;
   const int32_t lanes = k % (2 * vw) == 0 ? k / (2 * vw) : 0;
@@ -212,9 +335,17 @@ static int spmm_chunks(const pjds_dev *A, int32_t k, int vw) {
 template <typename TV, typename TX, bool PAT = false>
 static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cudaStream_t s) {
   constexpr int VW = V16<TX>::W;
-  const int ch = spmm_chunks(A, k, VW);
+  int ch = spmm_chunks(A, k, VW), pair_u = 0;
+  // block-structured matrices: one thread per pair of rows sharing their
+  // columns, two chunks per lane (bf16 from k = 8, fp32 at k = 8 and from
+  // k = 64); 4 jagged diagonals per round for bf16 values from k = 16, else 2
+  const bool pair_k = A->dtype == PJDS_BF16 ? k >= 8 : (k == 8 || k >= 64);
+  if (A->dtype != PJDS_F64 && shared_pairs(A) && pair_k && k % (2 * VW) == 0) {
+    ch = 2;
+    pair_u = A->dtype == PJDS_BF16 && k >= 16 ? 4 : 2;
+  }
   const int32_t lr = k / (VW * ch);
-  const int64_t threads = (int64_t)A->n_rows * lr;
+  const int64_t threads = (pair_u ? ((int64_t)A->n_rows + 1) / 2 : (int64_t)A->n_rows) * lr;
   const int64_t grid = (threads + BT - 1) / BT;
   if (grid <= 0) return PJDS_OK;
   if (grid > 0x7fffffffLL) return set_error(PJDS_EOVERFLOW, "grid too large");
@@ -242,13 +373,34 @@ static int launch_spmm(const pjds_dev *A, int32_t k, const void *X, void *Y, cud
     else                 \
       SPMM(IDX, SC, 1);  \
   } while (0)
-  if (small) {
+#define SPMMP(IDX, SC, CH, UU)                                                                                 \
+  spmm_pair_kernel<TV, TX, IDX, SC, CH, UU, PAT><<<(unsigned)grid, BT, 0, s>>>(val, A->col, A->col_start,        \
+                                                                            A->block_len, A->perm, x, y, A->n_rows, \
+                                                                            A->b, k, lr)
+#define SPMMP_CH(IDX, SC)      \
+  do {                         \
+    if (pair_u == 2)           \
+      SPMMP(IDX, SC, 2, 2);    \
+    else                       \
+      SPMMP(IDX, SC, 2, 4);    \
+  } while (0)
+  if (pair_u) {
+    if (small) {
+      if (sc) SPMMP_CH(int32_t, true);
+      else SPMMP_CH(int32_t, false);
+    } else {
+      if (sc) SPMMP_CH(int64_t, true);
+      else SPMMP_CH(int64_t, false);
+    }
+  } else if (small) {
     if (sc) SPMM_CH(int32_t, true);
     else SPMM_CH(int32_t, false);
   } else {
     if (sc) SPMM_CH(int64_t, true);
     else SPMM_CH(int64_t, false);
   }
+#undef SPMMP_CH
+#undef SPMMP
 #undef SPMM_CH
 #undef SPMM
   cudaError_t e = cudaGetLastError();

@@ -33,6 +33,14 @@ inline bool auto_tile_order(const pjds_dev *A) {
   return (int64_t)A->n_max * A->n_rows <= 4 * A->nnz;
 }
 
+// Block-structured matrix on which one thread takes both rows of a pair
+// (sorted rows 2k, 2k + 1): at least half the entries share the paired row's
+// column (pair_share >= 500), at least 2^18 rows and 64 entries per row on
+// average. The single product (fp32 / bf16) and the block product use it.
+inline bool shared_pairs(const pjds_dev *A) {
+  return A->pair_share >= 500 && A->n_rows >= (1 << 18) && A->nnz >= 64 * (int64_t)A->n_rows;
+}
+
 // Whether the per-tile mapping can run (a plan, 16-byte aligned plan, val and
 // col: the tiles of two and four rows per thread use vector loads).
 inline bool plan_usable(const pjds_dev *A) {

@@ -227,3 +227,60 @@ def test_dlr_default_paired_rows_full(P, oracle_lib, dtype):
     r = parity.check_fp32(y.double().cpu().numpy(), oracle_lib.crs_spmv(Ar, xd), oracle_lib.crs_absmv(Ar, xd),
                           np.diff(A.row_ptr))
     assert r["ok"], r
+
+
+def _partly_shared_dlr():
+    """The DLR-like matrix with entry 7 of every fifth row dropped: rows of 143
+    sort behind those of 144, so about half the pairs of sorted rows no longer
+    share their columns and some pairs hold rows of both lengths."""
+    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=1234)
+    drop = np.arange(A.n_rows) % 5 == 1
+    keep = np.ones(len(A.col), bool)
+    keep[A.row_ptr[:-1][drop] + 7] = False
+    rp = np.zeros(A.n_rows + 1, np.int64)
+    np.cumsum(np.diff(A.row_ptr) - drop, out=rp[1:])
+    return A._replace(row_ptr=rp, col=A.col[keep], val=A.val[keep])
+
+
+@pytest.mark.parametrize("which,dtype,k", [("dlr", "f32", 8), ("dlr", "f32", 64), ("dlr", "bf16", 16),
+                                           ("dlr", "bf16", 32), ("partly", "f32", 8), ("partly", "bf16", 32)])
+def test_spmm_paired_rows_full(P, oracle_lib, which, dtype, k):
+    # the block product with one thread per pair of rows (block-structured
+    # matrices, fp32 / bf16, k a multiple of 8): every element within the fp32
+    # bound, columns bit for bit the single product with one row per thread,
+    # and its pattern product (the gather ceiling) against the oracle's
+    import torch
+    from paper_1112_5588_gb300 import batch
+    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=1234) if which == "dlr" else \
+        _partly_shared_dlr()
+    H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype)
+    assert H.pair_share >= 500, H.pair_share
+    D = H.to_device("cuda")
+    H.destroy()
+    X = np.random.default_rng(k).uniform(-1, 1, (A.n_cols, k)).astype(np.float32)
+    Xt = torch.from_numpy(X).cuda()
+    Yt = torch.full((A.n_rows, k), float("nan"), device="cuda")
+    batch.spmm(D, Xt, Yt)
+    torch.cuda.synchronize()
+    Ar = A._replace(val=oracle_lib.round_f32(A.val) if dtype == "f32" else oracle_lib.round_bf16(A.val))
+    Xd = X.astype(np.float64)
+    Yr = oracle_lib.crs_spmm(Ar, Xd)
+    S = oracle_lib.crs_spmm(Ar._replace(val=np.abs(Ar.val)), np.abs(Xd))
+    Y = Yt.double().cpu().numpy()
+    lens = np.diff(A.row_ptr)
+    for c in range(k):
+        r = parity.check_fp32(Y[:, c], Yr[:, c], S[:, c], lens)
+        assert r["ok"], (c, r)
+    for c in (0, k - 1):
+        y1 = torch.empty(A.n_rows, device="cuda")
+        P.pjds_spmv_cfg(D, Xt[:, c].contiguous(), y1, threads_per_row=1, rows_per_thread=1)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, Yt[:, c].contiguous()), c
+    batch.spmm_pattern(D, Xt, Yt)
+    torch.cuda.synchronize()
+    ones = A._replace(val=np.ones_like(A.val))
+    Yp = oracle_lib.crs_spmm(ones, Xd)
+    Sp = oracle_lib.crs_spmm(ones, np.abs(Xd))
+    Y = Yt.double().cpu().numpy()
+    for c in (0, k // 2, k - 1):
+        assert parity.check_fp32(Y[:, c], Yp[:, c], Sp[:, c], lens)["ok"], c
