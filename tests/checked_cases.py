@@ -3,9 +3,10 @@ with PJDS_LIBRARY=checked, which loads libpjds_checked.so).
 
 Clean: every mapping of the product with device-side extent checks (one and
 T threads per row, several rows per thread, tile order, per-tile mapping,
-64-bit offsets), the pattern product, ELLPACK-R and the batched launch, on
-ragged, spread and banded matrices, must leave the check word at 0 and
-(fp64) match the oracle.
+64-bit offsets), the pattern product, ELLPACK-R, the block product (also with
+paired rows on a block-structured matrix) and the batched launch, on ragged,
+spread, banded and block-dense matrices, must leave the check word at 0 and
+match the oracle (fp64; fp32 bounds for the paired block product).
 
 Planted: an index put out of range in a device copy of a matrix (a column
 beyond n_cols, a perm entry beyond n_rows, a jagged-diagonal offset beyond
@@ -129,6 +130,41 @@ def main():
         B.destroy()
         res["clean"].append(["batch", "f64", 32, kw.get("lanes") and "lanes" or kw.get("rule") and "rule" or "default",
                              w, ok])
+
+    # paired rows (block-structured, 2^18 rows of 64: pair_share 1000): the
+    # single product (two rows per thread), the paired block product and its
+    # pattern product
+    Pm = synth.block_dense(70_000, 4, 16, 0.05, seed=67)
+    lens = np.diff(Pm.row_ptr)
+    for dt, k in (("f32", 8), ("bf16", 16)):
+        D = pjds.pjds_create(Pm.n_rows, Pm.n_cols, Pm.row_ptr, Pm.col, Pm.val, b=32, dtype=dt).to_device("cuda")
+        assert D.pair_share >= 500 and pjds.pjds_spmv_resolve(D)["rows_per_thread"] == 2
+        xt = torch.from_numpy(synth.vector(Pm.n_cols, seed=68)).to("cuda", D.vec_dtype)
+        y = run(D, xt, {})
+        res["clean"].append(["paired", dt, 32, "spmv", pjds.pjds_check_word(clear=True), bool(torch.isfinite(y).all())])
+        X = np.stack([synth.vector(Pm.n_cols, seed=80 + c) for c in range(k)], axis=1).astype(np.float32)
+        Xt = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        for fn, tag in ((batch.spmm, "spmm"), (batch.spmm_pattern, "spmm_pattern")):
+            Y = torch.full((Pm.n_rows, k), float("nan"), device="cuda")
+            fn(D, Xt, Y)
+            torch.cuda.synchronize()
+            w = pjds.pjds_check_word(clear=True)
+            ok = bool(torch.isfinite(Y).all())
+            if tag == "spmm":
+                Ar = Pm._replace(val=oracle.round_f32(Pm.val) if dt == "f32" else oracle.round_bf16(Pm.val))
+                Xd = X.astype(np.float64)
+                Yr, S = oracle.crs_spmm(Ar, Xd), oracle.crs_spmm(Ar._replace(val=np.abs(Ar.val)), np.abs(Xd))
+                Yg = Y.double().cpu().numpy()
+                ok = ok and all(parity.check_fp32(Yg[:, c], Yr[:, c], S[:, c], lens)["ok"] for c in (0, k - 1))
+            res["clean"].append(["paired", dt, 32, f"{tag} k={k}", w, ok])
+    # a column beyond n_cols in the paired block product: recorded and skipped
+    D = pjds.pjds_create(Pm.n_rows, Pm.n_cols, Pm.row_ptr, Pm.col, Pm.val, b=32, dtype="f32").to_device("cuda")
+    D.col[1] = Pm.n_cols + 11
+    Y = torch.empty(Pm.n_rows, 8, device="cuda")
+    batch.spmm(D, torch.rand(Pm.n_cols, 8, device="cuda"), Y)
+    torch.cuda.synchronize()
+    res["planted"]["paired_column"] = [[{}, *split(pjds.pjds_check_word(clear=True))]]
+    res["paired_n_cols"] = Pm.n_cols
 
     # planted indices (fp64, original basis)
     A = mats["ragged"]

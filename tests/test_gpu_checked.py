@@ -60,3 +60,10 @@ def test_planted_block_length_is_recorded(res):
     n = res["n"]
     for cfg, code, idx in res["planted"]["block"]:
         assert (code == DIAG and idx >= n["n_max"] + 1) or (code == OFFSET and idx >= n["n_stored"]), (cfg, code, idx)
+
+
+def test_paired_block_product_column_is_recorded(res):
+    # the block product with one thread per pair of rows checks both rows' columns
+    for cfg, code, idx in res["planted"]["paired_column"]:
+        assert (code, idx) == (COLUMN, res["paired_n_cols"] + 11), (cfg, code, idx)
+    assert any(c[0] == "paired" for c in res["clean"])
