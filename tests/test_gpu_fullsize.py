@@ -242,8 +242,17 @@ def _partly_shared_dlr():
     return A._replace(row_ptr=rp, col=A.col[keep], val=A.val[keep])
 
 
+def _odd_dlr():
+    """The DLR-like matrix with one more row (a single entry): an odd row count,
+    so the last pair of sorted rows holds one row."""
+    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=1234)
+    return A._replace(n_rows=A.n_rows + 1, row_ptr=np.append(A.row_ptr, A.row_ptr[-1] + 1),
+                      col=np.append(A.col, np.int32(5)), val=np.append(A.val, 0.75))
+
+
 @pytest.mark.parametrize("which,dtype,k", [("dlr", "f32", 8), ("dlr", "f32", 64), ("dlr", "bf16", 16),
-                                           ("dlr", "bf16", 32), ("partly", "f32", 8), ("partly", "bf16", 32)])
+                                           ("dlr", "bf16", 32), ("partly", "f32", 8), ("partly", "bf16", 32),
+                                           ("odd", "bf16", 16)])
 def test_spmm_paired_rows_full(P, oracle_lib, which, dtype, k):
     # the block product with one thread per pair of rows (block-structured
     # matrices, fp32 / bf16, k a multiple of 8): every element within the fp32
@@ -251,8 +260,8 @@ def test_spmm_paired_rows_full(P, oracle_lib, which, dtype, k):
     # and its pattern product (the gather ceiling) against the oracle's
     import torch
     from paper_1112_5588_gb300 import batch
-    A = synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=1234) if which == "dlr" else \
-        _partly_shared_dlr()
+    A = {"dlr": lambda: synth.block_dense(n_brow=70_000, bs=4, nb=36, frac=0.05, seed=1234),
+         "partly": _partly_shared_dlr, "odd": _odd_dlr}[which]()
     H = P.pjds_create(A.n_rows, A.n_cols, A.row_ptr, A.col, A.val, b=32, dtype=dtype)
     assert H.pair_share >= 500, H.pair_share
     D = H.to_device("cuda")
