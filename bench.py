@@ -941,6 +941,27 @@ def spread_leg(torch, pjds, args, dev, flush):
                              "live_regret": round(entries[pick["index"]]["us"] / t_best - 1, 4)}
         out[dt]["default_regret_in_sweep"] = round(entries[k_def]["us"] / t_best - 1, 4) if k_def >= 0 else None
         del D, x, y
+    # against ELLPACK-R (Table 1's comparison on spread row lengths, sAMG-like): a
+    # 200k-row Zipf matrix, fp64; ELLPACK-R pads every row to the longest
+    Z = synth.zipf_rows(200_000, s=2.0, len_max=512, seed=args.seed + 1)
+    Hz = pjds.pjds_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val, b=32)
+    Ez = pjds.ellr_create(Z.n_rows, Z.n_cols, Z.row_ptr, Z.col, Z.val)
+    stored = {"pjds": int(Hz.n_stored), "ellr": int(Ez.n_stored)}
+    Dz, Dez = Hz.to_device(dev), Ez.to_device(dev)
+    Hz.destroy()
+    Ez.destroy()
+    x = torch.from_numpy(synth.vector(Z.n_cols, seed=args.seed)).to(dev)
+    y, ye = torch.empty(Z.n_rows, dtype=torch.float64, device=dev), torch.empty(Z.n_rows, dtype=torch.float64, device=dev)
+    t_p = statistics.median(time_launches(torch, lambda: pjds.pjds_spmv(Dz, x, y), 10, 3, flush))
+    t_e = statistics.median(time_launches(torch, lambda: pjds.ellr_spmv(Dez, x, ye), 10, 3, flush))
+    pjds.pjds_spmv_cfg(Dz, x, y, threads_per_row=1, rows_per_thread=1, tile_order=-1)
+    torch.cuda.synchronize()
+    out["vs_ellpack_r"] = {"matrix": f"Zipf s=2 N={Z.n_rows} nnz={Z.nnz} (rows up to {int(np.diff(Z.row_ptr).max())}), fp64",
+                           "pjds_us": round(t_p * 1e6, 2), "ellr_us": round(t_e * 1e6, 2),
+                           "pjds_vs_ellr_speed": round(t_e / t_p, 3), "stored": stored,
+                           "pjds_data_reduction_vs_ellpack": round(1 - stored["pjds"] / stored["ellr"], 4),
+                           "bit_identical_one_thread_per_row": bool(torch.equal(y, ye))}
+    del Dz, Dez, x, y, ye
     torch.cuda.synchronize()
     return out
 
